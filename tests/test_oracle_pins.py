@@ -1,0 +1,271 @@
+"""Pins of the FP64 oracle against what theory fixes (CPU only).
+
+Each test ties the oracle to something other than itself:
+  * brute-force projections <mu|exp(-T) H exp(T)|0> in a determinant basis,
+  * exact two-electron FCI and Hellmann-Feynman derivatives (o = 1),
+  * the closed-form MP2 energy,
+  * central finite differences of the energy,
+  * invariances (orbital rotations, Cholesky-vector rotations, symmetry),
+  * Euler's theorem for the degree-2 homogeneity of the energy in L,
+  * a pivoted Cholesky factorisation (LAPACK dpstrf) of the ERI matrix.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+import torch
+
+from synth import (random_system, unpack_dense, pack_dense, make_system,
+                   make_displacements, make_displacement_nontotsym,
+                   irrep_split, chol_split)
+from oracle import brute, ccsd, model, lagrangian, fci2, mp2
+
+DT = torch.float64
+
+
+def T(x):
+    return torch.as_tensor(np.asarray(x), dtype=DT)
+
+
+def _sys_dense(s):
+    L = unpack_dense(s, s.L)
+    h = model.core_from_eps(T(s.eps), T(L), s.nocc)
+    return L, h
+
+
+def _random_amps(rng, o, v, scale=0.1):
+    t1 = rng.standard_normal((o, v)) * scale
+    t2 = rng.standard_normal((o, o, v, v)) * scale
+    return t1, 0.5 * (t2 + t2.transpose(1, 0, 3, 2))
+
+
+# ---------------------------------------------------------------- generator
+def test_generator_splits():
+    assert irrep_split(60, 8, "even") == [8, 8, 8, 8, 7, 7, 7, 7]
+    assert irrep_split(540, 8, "even") == [68] * 4 + [67] * 4
+    assert irrep_split(40, 4, (0.4, 0.25, 0.2, 0.15)) == [16, 10, 8, 6]
+    assert irrep_split(360, 4, (0.4, 0.25, 0.2, 0.15)) == [144, 90, 72, 54]
+    assert chol_split(1600, 4, [160, 100, 80, 60]) == [456, 416, 376, 352]
+    s = make_system(1)
+    assert s.chol == [80] * 8 and s.occ == [2] * 8 and s.vir == [18] * 8
+
+
+def test_pack_roundtrip_and_pattern():
+    s = random_system([2, 1, 1, 0], [3, 2, 1, 2], [5, 3, 4, 2], seed=3)
+    d = unpack_dense(s, s.L)
+    assert np.array_equal(pack_dense(s, d), s.L)
+    assert np.allclose(d, d.transpose(0, 2, 1))
+    for P in range(s.nchol):
+        for p in range(s.n):
+            for q in range(s.n):
+                if s.orb_irrep[p] ^ s.orb_irrep[q] != s.chol_irrep[P]:
+                    assert d[P, p, q] == 0.0
+
+
+# ---------------------------------------------------------------- Eq. 1
+def test_cholesky_reconstructs_eri():
+    s = random_system([1, 1], [2, 2], [4, 3], seed=11)
+    L = unpack_dense(s, s.L)
+    n = s.n
+    g = model.eri(T(L)).numpy()
+    M = g.reshape(n * n, n * n)
+    assert np.allclose(M, M.T, atol=1e-14)
+    # pivoted Cholesky of the ERI supermatrix: PSD, rank <= nL, exact
+    c, piv, rank, info = scipy.linalg.lapack.dpstrf(M + 0.0, lower=1,
+                                                    tol=1e-13)
+    assert rank <= s.nchol
+    Lc = np.tril(c)[:, :rank]
+    Pm = np.eye(n * n)[:, piv - 1]
+    assert np.abs(Pm @ Lc @ Lc.T @ Pm.T - M).max() < 1e-12
+    # selection rule: (pq|rs) = 0 unless irrep(pq) == irrep(rs)
+    ir = s.orb_irrep
+    for p in range(n):
+        for q in range(n):
+            for r in range(n):
+                for t in range(n):
+                    if ir[p] ^ ir[q] != ir[r] ^ ir[t]:
+                        assert g[p, q, r, t] == 0.0
+
+
+# ------------------------------------------------ amplitude equations (pin)
+CASES = [((2,), (3,), (6,), 1), ((1, 1), (2, 1), (3, 3), 2),
+         ((1,), (4,), (5,), 3), ((2, 1), (1, 1), (4, 2), 4)]
+
+
+@pytest.mark.parametrize("occ,vir,chol,seed", CASES)
+def test_residual_equals_determinant_projection(occ, vir, chol, seed):
+    s = random_system(list(occ), list(vir), list(chol), seed=seed, scale=0.8)
+    L = unpack_dense(s, s.L)
+    rng = np.random.default_rng(seed)
+    n, o, v = s.n, s.nocc, s.nvir
+    h = rng.standard_normal((n, n)) * 0.3
+    h = 0.5 * (h + h.T)                      # non-canonical, f_ia != 0
+    t1, t2 = _random_amps(rng, o, v, 0.15)
+    Eb, R1b, R2b = brute.projections(h, L, o, t1, t2)
+    R1, R2, E = ccsd.residual(T(t1), T(t2), T(h), T(L), o)
+    assert abs(E.item() - Eb) < 1e-12
+    assert np.abs(R1.numpy() - R1b).max() < 1e-12
+    assert np.abs(R2.numpy() - R2b).max() < 1e-12
+
+
+def test_planted_mistake_is_caught(monkeypatch):
+    """A 1% error in the ladder term must break the projection pin."""
+    s = random_system([2], [3], [5], seed=9, scale=0.8)
+    L = unpack_dense(s, s.L)
+    rng = np.random.default_rng(9)
+    h = np.diag(s.eps)
+    t1, t2 = _random_amps(rng, 2, 3, 0.2)
+    _, _, R2b = brute.projections(h, L, 2, t1, t2)
+    good = ccsd.ladder
+    monkeypatch.setattr(ccsd, "ladder", lambda t, vv: 0.99 * good(t, vv))
+    _, R2, _ = ccsd.residual(T(t1), T(t2), T(h), T(L), 2)
+    assert np.abs(R2.numpy() - R2b).max() > 1e-5
+
+
+def test_mp2_first_iteration():
+    s = random_system([3], [7], [10], seed=3, scale=0.5)
+    L, h = _sys_dense(s)
+    o, v = 3, 7
+    f = model.fock(h, T(L), o)
+    Dia, Dijab = ccsd.denominators(f, o)
+    z1, z2 = torch.zeros(o, v, dtype=DT), torch.zeros(o, o, v, v, dtype=DT)
+    R1, R2, _ = ccsd.residual(z1, z2, h, T(L), o)
+    assert (R1 / Dia).abs().max().item() < 1e-14      # f_ia = 0
+    e = ccsd.energy_corr(z1, R2 / Dijab, h, T(L), o)
+    assert abs(e - mp2.mp2_energy(s.eps, L, o)) < 1e-13
+
+
+# ------------------------------------------------ two electrons: CCSD = FCI
+@pytest.mark.parametrize("occ,vir,chol,seed", [((1,), (9,), (12,), 5),
+                                               ((1, 0, 0, 0), (3, 2, 2, 1),
+                                                (5, 3, 3, 3), 6)])
+def test_ccsd_is_fci_for_two_electrons(occ, vir, chol, seed):
+    s = random_system(list(occ), list(vir), list(chol), seed=seed, scale=0.6)
+    L, h = _sys_dense(s)
+    r = lagrangian.run_all(h, T(L), 1, tol=1e-12, e_tol=1e-13)
+    E_fci, C = fci2.singlet_fci(h.numpy(), L)
+    assert abs(r["cc"]["E"] - E_fci) < 1e-11
+    # Hellmann-Feynman with h fixed: the Lambda gradient is exact
+    dL = np.stack([unpack_dense(s, x) for x in make_displacements(s, 3)])
+    g = lagrangian.gradient_from_density(r["G"], T(dL)).numpy()
+    g_hf = fci2.hellmann_feynman(C, L, dL)
+    assert np.abs(g - g_hf).max() < 1e-11
+
+
+def test_two_electron_fci_matches_determinants():
+    s = random_system([1], [3], [4], seed=21, scale=0.7)
+    L, h = _sys_dense(s)
+    E_fci, _ = fci2.singlet_fci(h.numpy(), L)
+    assert abs(E_fci - brute.fci_ground_energy(h.numpy(), L, 1)) < 1e-12
+
+
+# ------------------------------------------------ gradient vs finite diff.
+def _fd_gradient(h, L, o, dL, steps=(1e-3, 5e-4)):
+    def energy(x):
+        return ccsd.solve_ccsd(h, T(L + x * dL), o, tol=1e-13,
+                               e_tol=1e-14)["E"]
+    fd = [(energy(s) - energy(-s)) / (2 * s) for s in steps]
+    return (4.0 * fd[1] - fd[0]) / 3.0            # Richardson
+
+
+@pytest.mark.parametrize("which", ["c0", "sym"])
+def test_gradient_matches_finite_difference(which):
+    if which == "c0":
+        s = make_system(0)
+        nx = 2
+    else:
+        s = random_system([2, 1, 1, 1], [4, 3, 3, 2], [8, 6, 6, 6], seed=13,
+                          scale=0.35)
+        nx = 2
+    L, h = _sys_dense(s)
+    o = s.nocc
+    dL = np.stack([unpack_dense(s, x) for x in make_displacements(s, nx)])
+    r = lagrangian.run_all(h, T(L), o, tol=1e-12, e_tol=1e-13)
+    g = lagrangian.gradient_from_density(r["G"], T(dL)).numpy()
+    for x in range(nx):
+        assert abs(g[x] - _fd_gradient(h, L, o, dL[x])) < 1e-8
+
+
+# ------------------------------------------------ symmetry
+def test_non_totally_symmetric_displacement_gives_zero():
+    s = random_system([1, 1, 1, 0], [3, 2, 2, 2], [6, 4, 4, 4], seed=17,
+                      scale=0.5)
+    L, h = _sys_dense(s)
+    r = lagrangian.run_all(h, T(L), s.nocc, tol=1e-11)
+    G = r["G"]
+    for gx in (1, 2, 3):
+        dL = unpack_dense(s, make_displacement_nontotsym(s, gx), gx=gx)
+        assert np.abs(dL).max() > 0
+        g = lagrangian.gradient_from_density(G, T(dL[None])).item()
+        assert abs(g) < 1e-13
+    # densities and amplitudes respect the selection rule
+    ir, cir, o = s.orb_irrep, s.chol_irrep, s.nocc
+    Gn = G.numpy()
+    mask = (ir[None, :, None] ^ ir[None, None, :]) != cir[:, None, None]
+    assert np.abs(Gn[mask]).max() < 1e-14
+    t2 = r["cc"]["t2"].numpy()
+    io, iv = ir[:o], ir[o:]
+    m2 = (io[:, None, None, None] ^ io[None, :, None, None]
+          ^ iv[None, None, :, None] ^ iv[None, None, None, :]) != 0
+    assert np.abs(t2[m2]).max() < 1e-14
+
+
+def test_lambda_is_symmetric():
+    s = random_system([2], [4], [6], seed=31, scale=0.5)
+    L, h = _sys_dense(s)
+    r = lagrangian.run_all(h, T(L), 2, tol=1e-11)
+    l2 = r["lam"]["l2"]
+    assert (l2 - l2.permute(1, 0, 3, 2)).abs().max().item() < 1e-13
+
+
+# ------------------------------------------------ invariances
+def _rot(rng, k):
+    q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    return q
+
+
+def test_orbital_rotation_invariance():
+    s = random_system([3], [6], [9], seed=41, scale=0.5)
+    L, h = _sys_dense(s)
+    o, n = 3, s.n
+    dL = unpack_dense(s, make_displacements(s, 1)[0])
+    r0 = lagrangian.run_all(h, T(L), o, tol=1e-12, e_tol=1e-13)
+    g0 = lagrangian.gradient_from_density(r0["G"], T(dL[None])).item()
+    rng = np.random.default_rng(5)
+    U = scipy.linalg.block_diag(_rot(rng, o), _rot(rng, n - o))
+    Lr = np.einsum("pi,Ppq,qj->Pij", U, L, U)
+    dLr = np.einsum("pi,Ppq,qj->Pij", U, dL, U)
+    hr = T(U.T @ h.numpy() @ U)
+    r1 = lagrangian.run_all(hr, T(Lr), o, tol=1e-12, e_tol=1e-13)
+    g1 = lagrangian.gradient_from_density(r1["G"], T(dLr[None])).item()
+    assert abs(r0["cc"]["E"] - r1["cc"]["E"]) < 1e-11
+    assert abs(g0 - g1) < 1e-10
+
+
+def test_cholesky_vector_rotation_invariance():
+    """The CD is not unique (Sec. 2.1): any orthogonal mixing of the vectors
+    leaves (pq|rs), hence E and the gradient, unchanged."""
+    s = random_system([2], [5], [7], seed=43, scale=0.5)
+    L, h = _sys_dense(s)
+    dL = np.stack([unpack_dense(s, x) for x in make_displacements(s, 2)])
+    O = _rot(np.random.default_rng(3), s.nchol)
+    r0 = lagrangian.run_all(h, T(L), 2, tol=1e-12, e_tol=1e-13)
+    r1 = lagrangian.run_all(h, T(np.einsum("PQ,Qpq->Ppq", O, L)), 2,
+                            tol=1e-12, e_tol=1e-13)
+    g0 = lagrangian.gradient_from_density(r0["G"], T(dL)).numpy()
+    g1 = lagrangian.gradient_from_density(
+        r1["G"], T(np.einsum("PQ,xQpq->xPpq", O, dL))).numpy()
+    assert abs(r0["cc"]["E"] - r1["cc"]["E"]) < 1e-11
+    assert np.abs(g0 - g1).max() < 1e-10
+
+
+def test_euler_identity():
+    """With the densities fixed, the energy is homogeneous of degree 2 in L:
+    sum_P <Gamma^P, L^P> = 2 (E - sum_pq D_pq h_pq)."""
+    s = random_system([2, 1], [4, 3], [6, 5], seed=47, scale=0.5)
+    L, h = _sys_dense(s)
+    r = lagrangian.run_all(h, T(L), s.nocc, tol=1e-12, e_tol=1e-13)
+    lhs = float(np.sum(r["G"].numpy() * L))
+    rhs = 2.0 * (r["cc"]["E"] - float(np.sum(r["D"].numpy() * h.numpy())))
+    assert abs(lhs - rhs) < 1e-11
+    # the 1-RDM traces to the electron count
+    assert abs(np.trace(r["D"].numpy()) - 2 * s.nocc) < 1e-11
