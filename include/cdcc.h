@@ -1,0 +1,179 @@
+/*
+ * cdcc.h -- C ABI of the GB300 CD-CCSD gradient library.
+ *
+ * Closed-shell CCSD analytic gradients with Cholesky-decomposed integrals and
+ * Abelian point-group symmetry (arXiv 2512.21909).  The library solves the
+ * CCSD amplitude equations, the Lambda equations (Sec. 2.3), builds the
+ * Cholesky-basis density Gamma^P_pq (Sec. 2.4 and 2.6) and contracts it with
+ * derivative Cholesky vectors (Sec. 2.1, Eq. 2):
+ *     dE/dx = sum_P sum_pq Gamma^P_pq dL^P_pq/dx .
+ *
+ * Conventions shared by every entry point
+ *   - Irreps of the Abelian group are 0..h-1 (h = 1, 2, 4 or 8) in the Z2^k
+ *     ordering; the direct product is bitwise XOR (Sec. 3.1).
+ *   - Orbitals: n = nocc + nvir; the first nocc are occupied.  Within the
+ *     occupied and within the virtual range the orbitals must be sorted by
+ *     irrep (non-decreasing label).  Cholesky vectors must be sorted by
+ *     irrep.  Violations return CDCC_EINVAL.
+ *   - Packed Cholesky layout ("L-pattern") for L, dL and Gamma:
+ *         for G_P in 0..h-1, for each vector P of irrep G_P,
+ *           for G_p in 0..h-1 with G_q = G_p ^ G_P ^ G_x:
+ *             the block L^P[p][q], p over the orbitals of irrep G_p and q over
+ *             those of irrep G_q (ascending orbital order), row-major.
+ *     G_x is the irrep of a displacement (0 for L and Gamma).  Its length is
+ *     cdcc_packed_size(ctx, G_x) doubles.
+ *   - Buffers: every pointer argument may be host memory or device memory of
+ *     the context's device; the library detects which.  The caller owns all
+ *     buffers; inputs are copied before the call returns (or, for device
+ *     inputs, before the call's work is enqueued), outputs are written
+ *     before the call returns.  The library never keeps a caller pointer.
+ *   - Device memory: the context owns its device memory.  It is obtained
+ *     through cdcc_options.dev_alloc / dev_free when set (a caching
+ *     allocator such as PyTorch's), else with cudaMallocAsync.
+ *   - Work runs on cdcc_options.stream (0 = the legacy default stream); every
+ *     call synchronises that stream before returning a result to the host.
+ *   - Errors: every call returns a cdcc_status; cdcc_last_error() gives a
+ *     message.  After CDCC_ECUDA the context must be freed; after any other
+ *     non-OK status the context stays usable.  Calls out of order return
+ *     CDCC_ESTATE.  One context must not be used by two threads at once.
+ */
+#ifndef CDCC_H
+#define CDCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CDCC_OK = 0,
+    CDCC_EINVAL = 1,    /* invalid argument or input data                  */
+    CDCC_ENOMEM = 2,    /* device or host allocation failed                */
+    CDCC_ENOCONV = 3,   /* iterations did not converge within max_iter     */
+    CDCC_ENUMERIC = 4,  /* NaN / Inf in a residual norm                    */
+    CDCC_ECUDA = 5,     /* CUDA runtime error; the context is unusable     */
+    CDCC_ESTATE = 6,    /* call out of order                               */
+    CDCC_ETIMEOUT = 7   /* a bounded device wait gave up                   */
+} cdcc_status;
+
+/* Arithmetic of the dense contractions.                                   */
+typedef enum {
+    CDCC_PREC_FP64 = 0,   /* every contraction in FP64 (DFMA)              */
+    CDCC_PREC_MIXED = 1   /* split-precision tensor-core contractions with
+                             an FP64 finish (see cdcc_options)             */
+} cdcc_precision;
+
+typedef void *(*cdcc_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*cdcc_free_fn)(void *ptr, size_t bytes, void *stream,
+                             void *user);
+
+typedef struct {
+    double conv_tol;        /* max |R/D| convergence (default 1e-10)        */
+    double energy_tol;      /* |dE| convergence of CCSD (default 1e-12)     */
+    int max_iter;           /* per solver (default 100)                     */
+    int diis_dim;           /* DIIS vectors, 0 disables (default 8)         */
+    int precision;          /* cdcc_precision (default CDCC_PREC_FP64)      */
+    double switch_tol;      /* MIXED: max |R/D| below which the FP64
+                               contractions take over (default 1e-6)        */
+    int device;             /* CUDA device ordinal (default 0)              */
+    void *stream;           /* cudaStream_t (default 0)                     */
+    cdcc_alloc_fn dev_alloc;/* optional device allocator                    */
+    cdcc_free_fn dev_free;
+    void *alloc_user;
+} cdcc_options;
+
+typedef struct cdcc_ctx cdcc_ctx;
+
+/* Fill *opt with the defaults above. */
+void cdcc_default_options(cdcc_options *opt);
+
+/*
+ * Create a context from the model Hamiltonian (problem statement of
+ * Sec. 2.1 / 2.2 for a synthetic MO basis).
+ *   nirrep       1, 2, 4 or 8
+ *   nocc, nvir   orbital counts (nocc >= 1, nvir >= 1)
+ *   nchol        number of Cholesky vectors (>= 1)
+ *   orb_irrep    [nocc+nvir] int32 irrep of each orbital (sorted, see above)
+ *   eps          [nocc+nvir] double orbital energies; max eps_occ must be
+ *                below min eps_vir
+ *   chol_irrep   [nchol] int32 irrep of each vector (sorted)
+ *   L            packed Cholesky vectors (L-pattern, G_x = 0), symmetric in
+ *                pq: L^P_pq = L^P_qp within the stored blocks
+ *   opt          NULL = defaults
+ * The core Hamiltonian is fixed at h = diag(eps) - G(L) (the Fock matrix of
+ * the closed-shell determinant is diag(eps)); displacements change L only.
+ */
+cdcc_status cd_ccsd_init(cdcc_ctx **out, int nirrep, int nocc, int nvir,
+                         int nchol, const int32_t *orb_irrep,
+                         const double *eps, const int32_t *chol_irrep,
+                         const double *L, const cdcc_options *opt);
+
+/* Number of doubles of a packed Cholesky-pattern tensor of irrep gx. */
+size_t cdcc_packed_size(const cdcc_ctx *ctx, int gx);
+
+/*
+ * Solve the CCSD amplitude equations (T1/T2; the PPL of Sec. 2.3 is built
+ * on the fly from L^P_ab).  Outputs (any may be NULL): correlation energy,
+ * iteration count, final max |R/D|.
+ */
+cdcc_status ccsd_solve(cdcc_ctx *ctx, double *e_corr, int *iters,
+                       double *resid);
+
+/*
+ * Solve the Lambda equations dLag/dt = 0 (Sec. 2.3).  Requires ccsd_solve.
+ */
+cdcc_status lambda_solve(cdcc_ctx *ctx, int *iters, double *resid);
+
+/*
+ * Build the densities (Sec. 2.4): Gamma^P_pq = dLag/dL^P_pq (symmetrised,
+ * kept on the device in the packed L-pattern) and, if D1 != NULL, the
+ * one-particle density D_pq = dLag/dh_pq as a dense [n][n] row-major array.
+ * Requires lambda_solve.
+ */
+cdcc_status build_density(cdcc_ctx *ctx, double *D1);
+
+/* Copy Gamma^P_pq (packed L-pattern, cdcc_packed_size(ctx,0) doubles). */
+cdcc_status cdcc_get_gamma(cdcc_ctx *ctx, double *gamma);
+
+/*
+ * g[x] = sum_P sum_pq Gamma^P_pq dL_x^P_pq  (Sec. 2.1 Eq. 2, Sec. 2.6).
+ *   nx        number of displacements
+ *   x_irrep   [nx] irrep of each displacement (NULL = all totally
+ *             symmetric).  Displacement x is stored with the L-pattern of
+ *             irrep x_irrep[x]; for x_irrep[x] != 0 the gradient vanishes by
+ *             symmetry (Sec. 3.1) and g[x] = 0 is returned without reading.
+ *   dL        the nx packed tensors, back to back
+ *   g         [nx] output
+ * Requires build_density.
+ */
+cdcc_status contract_dL(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
+                        const double *dL, double *g);
+
+/* Everything that has not run yet, then contract_dL. */
+cdcc_status gradient(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
+                     const double *dL, double *e_corr, double *g);
+
+/* Amplitude / multiplier export for checks and warm starts:
+ * which = 0: t1 [nocc][nvir], 1: t2 [nocc][nocc][nvir][nvir],
+ *         2: lambda1, 3: lambda2 (same shapes; dense, zeros off-symmetry).
+ * Index conventions of t2: amplitude of a+_{a,alpha} a+_{b,beta} a_{j,beta}
+ * a_{i,alpha} at [i][j][a][b] (orbital indices relative to the occupied /
+ * virtual range).                                                         */
+cdcc_status cdcc_get_amplitudes(cdcc_ctx *ctx, int which, double *out);
+
+/* Wall-clock seconds of the last ccsd / lambda / density / contract_dL
+ * phases (device time of the stream, CUDA events). */
+cdcc_status cdcc_phase_times(cdcc_ctx *ctx, double *t4);
+
+/* Number of kernels this context has launched so far. */
+long long cdcc_kernel_launches(const cdcc_ctx *ctx);
+
+const char *cdcc_last_error(const cdcc_ctx *ctx);
+void cd_ccsd_free(cdcc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDCC_H */

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of include/cdcc.h (argument marshalling only).
+
+Every compute step runs inside libcdcc.so.  Inputs may be numpy arrays (host)
+or CUDA torch tensors (device); outputs are numpy arrays.  Device memory of
+a context comes from PyTorch's caching allocator and work runs on the
+current torch stream unless options say otherwise.  There is no CPU
+fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+_lib = None
+
+CDCC_OK, CDCC_EINVAL, CDCC_ENOMEM, CDCC_ENOCONV, CDCC_ENUMERIC, CDCC_ECUDA, \
+    CDCC_ESTATE, CDCC_ETIMEOUT = range(8)
+STATUS = {0: "CDCC_OK", 1: "CDCC_EINVAL", 2: "CDCC_ENOMEM", 3: "CDCC_ENOCONV",
+          4: "CDCC_ENUMERIC", 5: "CDCC_ECUDA", 6: "CDCC_ESTATE",
+          7: "CDCC_ETIMEOUT"}
+PREC_FP64, PREC_MIXED = 0, 1
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                            ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t,
+                           ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cdcc_options(ctypes.Structure):
+    _fields_ = [("conv_tol", ctypes.c_double), ("energy_tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("diis_dim", ctypes.c_int),
+                ("precision", ctypes.c_int), ("switch_tol", ctypes.c_double),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_user", ctypes.c_void_p)]
+
+
+class CdccError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return LIB
+
+
+def load():
+    """Load libcdcc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(
+            f"libcdcc.so not found at {LIB}: build it with "
+            "`python -m paper_2512_21909_gb300.build` (no CPU fallback)")
+    L = ctypes.CDLL(LIB)
+    P = ctypes.POINTER
+    vp, i32p, dp = ctypes.c_void_p, P(ctypes.c_int32), ctypes.c_void_p
+    L.cdcc_default_options.argtypes = [P(cdcc_options)]
+    L.cd_ccsd_init.argtypes = [P(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, vp, vp, vp, vp, P(cdcc_options)]
+    L.cdcc_packed_size.argtypes = [vp, ctypes.c_int]
+    L.cdcc_packed_size.restype = ctypes.c_size_t
+    L.ccsd_solve.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_int),
+                             P(ctypes.c_double)]
+    L.lambda_solve.argtypes = [vp, P(ctypes.c_int), P(ctypes.c_double)]
+    L.build_density.argtypes = [vp, vp]
+    L.cdcc_get_gamma.argtypes = [vp, vp]
+    L.contract_dL.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    L.gradient.argtypes = [vp, ctypes.c_int, vp, vp, P(ctypes.c_double), vp]
+    L.cdcc_get_amplitudes.argtypes = [vp, ctypes.c_int, vp]
+    L.cdcc_phase_times.argtypes = [vp, vp]
+    L.cdcc_kernel_launches.argtypes = [vp]
+    L.cdcc_kernel_launches.restype = ctypes.c_longlong
+    L.cdcc_last_error.argtypes = [vp]
+    L.cdcc_last_error.restype = ctypes.c_char_p
+    L.cd_ccsd_free.argtypes = [vp]
+    L.cd_ccsd_free.restype = None
+    for name in ("cd_ccsd_init", "ccsd_solve", "lambda_solve",
+                 "build_density", "cdcc_get_gamma", "contract_dL", "gradient",
+                 "cdcc_get_amplitudes", "cdcc_phase_times"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+# ------------------------------------------------------------------ helpers
+def _ptr(x):
+    """(pointer, keepalive) for a numpy array or a torch tensor."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), x
+    return ctypes.c_void_p(x.ctypes.data), x
+
+
+def _f64(x):
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64:
+            raise ValueError("expected float64")
+        return x
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _i32(x):
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+_KEEP = {}
+
+
+def _torch_allocator(device):
+    import torch
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device,
+                                                      stream or 0)
+        except Exception:
+            return None
+
+    def free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
+class Context:
+    """Owns a cdcc_ctx*; freed on close() / garbage collection."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    @property
+    def value(self):
+        return self.handle.value
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load().cd_ccsd_free(self.handle)
+            _KEEP.pop(id(self), None)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check(ctx, status):
+    if status != CDCC_OK:
+        msg = load().cdcc_last_error(ctx.handle if ctx else None)
+        raise CdccError(status, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------ the C ABI
+def cdcc_default_options() -> cdcc_options:
+    o = cdcc_options()
+    load().cdcc_default_options(ctypes.byref(o))
+    return o
+
+
+def cd_ccsd_init(nirrep, nocc, nvir, nchol, orb_irrep, eps, chol_irrep, L,
+                 options: cdcc_options | None = None, use_torch_memory=True,
+                 stream=None) -> Context:
+    lib = load()
+    opt = options if options is not None else cdcc_default_options()
+    keep = []
+    if use_torch_memory:
+        import torch
+        dev = opt.device
+        fa, ff = _torch_allocator(dev)
+        opt.dev_alloc, opt.dev_free = fa, ff
+        keep += [fa, ff]
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+    if stream is not None:
+        opt.stream = ctypes.c_void_p(int(stream))
+    oi, ci = _i32(orb_irrep), _i32(chol_irrep)
+    e = _f64(eps)
+    Lp, Lk = _ptr(_f64(L))
+    keep += [opt]
+    h = ctypes.c_void_p()
+    st = lib.cd_ccsd_init(ctypes.byref(h), int(nirrep), int(nocc), int(nvir),
+                          int(nchol), oi.ctypes.data_as(ctypes.c_void_p),
+                          e.ctypes.data_as(ctypes.c_void_p),
+                          ci.ctypes.data_as(ctypes.c_void_p), Lp,
+                          ctypes.byref(opt))
+    ctx = Context(h, keep)
+    _KEEP[id(ctx)] = keep
+    if st != CDCC_OK:
+        msg = lib.cdcc_last_error(h).decode()
+        ctx.close()
+        raise CdccError(st, msg)
+    return ctx
+
+
+def cdcc_packed_size(ctx, gx=0) -> int:
+    return int(load().cdcc_packed_size(ctx.handle, int(gx)))
+
+
+def ccsd_solve(ctx):
+    e, it, r = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    _check(ctx, load().ccsd_solve(ctx.handle, ctypes.byref(e), ctypes.byref(it),
+                                  ctypes.byref(r)))
+    return e.value, it.value, r.value
+
+
+def lambda_solve(ctx):
+    it, r = ctypes.c_int(), ctypes.c_double()
+    _check(ctx, load().lambda_solve(ctx.handle, ctypes.byref(it),
+                                    ctypes.byref(r)))
+    return it.value, r.value
+
+
+def build_density(ctx, n=None):
+    D1 = None if n is None else np.zeros((n, n))
+    _check(ctx, load().build_density(
+        ctx.handle, None if D1 is None else D1.ctypes.data_as(ctypes.c_void_p)))
+    return D1
+
+
+def cdcc_get_gamma(ctx):
+    out = np.empty(cdcc_packed_size(ctx, 0))
+    _check(ctx, load().cdcc_get_gamma(ctx.handle,
+                                      out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def _displacements(dL, x_irrep, nx):
+    if x_irrep is None:
+        xi = None
+        xp = None
+    else:
+        xi = _i32(x_irrep)
+        xp = xi.ctypes.data_as(ctypes.c_void_p)
+    d = _f64(dL)
+    dp, _ = _ptr(d)
+    return xi, xp, d, dp
+
+
+def contract_dL(ctx, dL, nx=None, x_irrep=None):
+    if nx is None:
+        nx = dL.shape[0] if getattr(dL, "ndim", 1) > 1 else 1
+    xi, xp, d, dp = _displacements(dL, x_irrep, nx)
+    g = np.zeros(nx)
+    _check(ctx, load().contract_dL(ctx.handle, int(nx), xp, dp,
+                                   g.ctypes.data_as(ctypes.c_void_p)))
+    return g
+
+
+def gradient(ctx, dL, nx=None, x_irrep=None):
+    if nx is None:
+        nx = dL.shape[0] if getattr(dL, "ndim", 1) > 1 else 1
+    xi, xp, d, dp = _displacements(dL, x_irrep, nx)
+    g = np.zeros(nx)
+    e = ctypes.c_double()
+    _check(ctx, load().gradient(ctx.handle, int(nx), xp, dp, ctypes.byref(e),
+                                g.ctypes.data_as(ctypes.c_void_p)))
+    return e.value, g
+
+
+def cdcc_get_amplitudes(ctx, which, nocc, nvir):
+    shape = (nocc, nvir) if which % 2 == 0 else (nocc, nocc, nvir, nvir)
+    out = np.zeros(shape)
+    _check(ctx, load().cdcc_get_amplitudes(ctx.handle, int(which),
+                                           out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def cdcc_phase_times(ctx):
+    t = np.zeros(4)
+    _check(ctx, load().cdcc_phase_times(ctx.handle,
+                                        t.ctypes.data_as(ctypes.c_void_p)))
+    return t
+
+
+def cdcc_kernel_launches(ctx) -> int:
+    return int(load().cdcc_kernel_launches(ctx.handle))
+
+
+def cdcc_last_error(ctx) -> str:
+    return load().cdcc_last_error(ctx.handle).decode()
+
+
+def cd_ccsd_free(ctx):
+    ctx.close()
+
+
+def init_from_system(sysm, **kw) -> Context:
+    """cd_ccsd_init from a synth.System (host arrays)."""
+    return cd_ccsd_init(sysm.nirrep, sysm.nocc, sysm.nvir, sysm.nchol,
+                        sysm.orb_irrep, sysm.eps, sysm.chol_irrep, sysm.L, **kw)

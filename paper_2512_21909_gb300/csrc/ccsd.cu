@@ -1,0 +1,970 @@
+// ccsd.cu -- closed-shell CD-CCSD residual, Lambda and density on the GPU,
+// and the C ABI of include/cdcc.h.
+//
+// Amplitude equations (T1-dressed form).  With t_ai = t1[i,a], the
+// similarity-transformed Hamiltonian exp(-T1) H exp(T1) has Cholesky vectors
+// Lhat^P = (1 - t) L^P (1 + t) (the t1-contracted intermediates t^P_ia,
+// t^P_ai, t^P_ij, t^P_ab of App. A folded into one dressed vector) and
+// one-electron part (1-t) h (1+t).  The residuals are the projections
+//     R1[i,a]     = < Phi_{i alpha}^{a alpha} | exp(-T) H exp(T) | 0 >
+//     R2[i,j,a,b] = < Phi_{i alpha j beta}^{a alpha b beta} | ... | 0 >
+// written with Cholesky-built integrals (Sec. 2.1 Eq. 1); the particle-
+// particle ladder (Sec. 2.3) uses (ac|bd) = sum_P Lhat^P_ac Lhat^P_bd.
+//
+// Lambda (Sec. 2.3): with Lag = E + l1.R1 + l2.R2 (Sec. 2.2), the Lambda
+// equations dLag/dt = 0 are solved by Jacobi/DIIS; dLag/dt is the reverse
+// (adjoint) sweep of the recorded residual, i.e. the transpose of every
+// residual contraction, evaluated with the t-dependent intermediates stored
+// once (they do not depend on lambda).
+//
+// Densities (Sec. 2.4, 2.6): Gamma^P_pq = dLag/dL^P_pq and D_pq = dLag/dh_pq
+// are one more reverse sweep with respect to the Cholesky vectors and h; the
+// vvvv part of the density is contracted on the fly with the Cholesky vectors
+// (the adjoint of the ladder), never stored as Gamma_abcd.
+// Gradient (Sec. 2.1 Eq. 2 + Sec. 2.6): g_x = sum_P sum_pq Gamma^P_pq dL_x^P_pq.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/cdcc.h"
+#include "engine.h"
+#include "kernels.h"
+
+using namespace cdcc;
+
+namespace {
+
+struct HostDims {
+  int h, nocc, nvir, n, nchol;
+};
+
+// dense index of local index l of irrep g in space s
+inline int64_t dense_index(const Dims& d, int s, int g, int l, int nocc) {
+  switch (s) {
+    case SO:
+    case SV:
+    case SQ:
+      return d.gstart[s][g] + l;
+    default:  // SA: orbital index
+      if (l < d.n[SO][g]) return d.gstart[SO][g] + l;
+      return nocc + d.gstart[SV][g] + (l - d.n[SO][g]);
+  }
+}
+
+inline int64_t dense_dim(const Dims& d, int s) {
+  if (s == SA) return d.total(SO) + d.total(SV);
+  return d.total(s);
+}
+
+// Visit every stored element of a DPD layout with its dense row-major index.
+template <class F>
+void visit_dense(const Layout& L, const Dims& d, F f) {
+  const int nocc = d.total(SO);
+  int64_t dd[MAXRANK];
+  for (int q = 0; q < L.rank; ++q) dd[q] = dense_dim(d, L.sp[q]);
+  for_each_tuple(d.h, L.rank, L.gtot, [&](const int* g) {
+    SubBlock sb = sub_block(L, d, g);
+    if (sb.empty) return;
+    int64_t n = 1;
+    for (int q = 0; q < L.rank; ++q) n *= sb.dim[q];
+    for (int64_t e = 0; e < n; ++e) {
+      int64_t r = e, off = sb.base, dense = 0;
+      int l[MAXRANK];
+      for (int q = L.rank - 1; q >= 0; --q) {
+        l[q] = (int)(r % sb.dim[q]);
+        r /= sb.dim[q];
+        off += l[q] * sb.stride[q];
+      }
+      for (int q = 0; q < L.rank; ++q)
+        dense = dense * dd[q] + dense_index(d, L.sp[q], g[q], l[q], nocc);
+      f(off, dense);
+    }
+  });
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Diis {
+  int dim = 0, count = 0, next = 0;
+  int64_t n = 0;
+  std::vector<Tensor*> x, e;
+  std::vector<double> B;  // dim x dim
+};
+
+}  // namespace
+
+struct cdcc_ctx {
+  cdcc_options opt;
+  Dims dims;
+  HostDims hd;
+  std::vector<int> orb_irrep, chol_irrep;
+  std::vector<double> eps;
+  cudaStream_t st = 0;
+  std::unique_ptr<Engine> eng;
+  std::string err;
+  int state = 0;  // 1 init, 2 ccsd, 3 lambda, 4 density
+  bool tape_ready = false;
+  double e_corr = 0, e_ref = 0;
+  int64_t nnz0 = 0;
+  double* d_eps = nullptr;
+  unsigned long long* d_max = nullptr;
+  double* d_dots = nullptr;
+  double* d_partial = nullptr;
+  int64_t partial_n = 0;
+  double phase[4] = {0, 0, 0, 0};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // tensors
+  Tensor *Lpk = nullptr, *Loo, *Lov, *Lvo, *Lvv;
+  Tensor *hoo, *hov, *hvo, *hvv, *Ioo;
+  Tensor *amp, *T1, *T2, *res, *R1, *R2, *err1, *lam, *L1, *L2, *E;
+  Tensor *Gam = nullptr, *Gsym = nullptr, *D1a = nullptr, *D1s = nullptr;
+  Diis cc_diis, lam_diis;
+};
+
+namespace {
+
+#define CK(x)                                                              \
+  do {                                                                     \
+    cudaError_t e_ = (x);                                                  \
+    if (e_ != cudaSuccess)                                                 \
+      throw EngineError(std::string("CUDA: ") + cudaGetErrorString(e_) +  \
+                        " at " #x);                                        \
+  } while (0)
+
+struct StatusError : std::exception {
+  cdcc_status s;
+  std::string m;
+  StatusError(cdcc_status s_, std::string m_) : s(s_), m(std::move(m_)) {}
+};
+
+void copy_in(cdcc_ctx* c, double* dst, const double* src, int64_t n) {
+  if (n <= 0) return;
+  CK(cudaMemcpyAsync(dst, src, (size_t)n * 8,
+                     is_device_ptr(src) ? cudaMemcpyDeviceToDevice
+                                        : cudaMemcpyHostToDevice,
+                     c->st));
+}
+
+std::vector<double> to_host(cdcc_ctx* c, const Tensor* t) {
+  std::vector<double> h((size_t)std::max<int64_t>(t->lay.size, 0));
+  if (!h.empty())
+    CK(cudaMemcpyAsync(h.data(), t->d, h.size() * 8, cudaMemcpyDeviceToHost,
+                       c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return h;
+}
+
+void upload_dense(cdcc_ctx* c, Tensor* t, const std::vector<double>& dense) {
+  std::vector<double> p((size_t)t->lay.size, 0.0);
+  visit_dense(t->lay, c->dims, [&](int64_t off, int64_t di) {
+    p[off] = dense[di];
+  });
+  CK(cudaMemcpyAsync(t->d, p.data(), p.size() * 8, cudaMemcpyHostToDevice,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+}
+
+// ------------------------------------------------------------------ residual
+// Forward evaluation of E, R1, R2 at the amplitudes in c->amp.  Every line is
+// one engine primitive so that the same code, recorded, yields the adjoints.
+void residual(cdcc_ctx* c) {
+  Engine& e = *c->eng;
+  auto T = [&](const char* n, std::vector<int> sp, int split) {
+    return e.tensor(n, sp, split);
+  };
+  Tensor *T1 = c->T1, *T2 = c->T2;
+  Tensor *Loo = c->Loo, *Lov = c->Lov, *Lvo = c->Lvo, *Lvv = c->Lvv;
+
+  // symmetrised doubles  t2s = (t2 + t2^swap) / 2
+  Tensor* t2s = T("t2s", {SO, SO, SV, SV}, 2);
+  e.axpy(0.5, T2, "ijab", 0.0, t2s, "ijab");
+  e.axpy(0.5, T2, "jiba", 1.0, t2s, "ijab");
+
+  // T1 dressing of the Cholesky vectors and of h
+  Tensor* Lhoo = T("Lhoo", {SQ, SO, SO}, 1);
+  e.axpy(1.0, Loo, "Pij", 0.0, Lhoo, "Pij");
+  e.contract(1.0, Lov, "Pia", T1, "ja", 1.0, Lhoo, "Pij");
+  Tensor* Lhvv = T("Lhvv", {SQ, SV, SV}, 1);
+  e.axpy(1.0, Lvv, "Pab", 0.0, Lhvv, "Pab");
+  e.contract(-1.0, T1, "ia", Lov, "Pib", 1.0, Lhvv, "Pab");
+  Tensor* Lhvo = T("Lhvo", {SQ, SV, SO}, 1);
+  e.axpy(1.0, Lvo, "Pai", 0.0, Lhvo, "Pai");
+  e.contract(1.0, Lvv, "Pab", T1, "ib", 1.0, Lhvo, "Pai");
+  e.contract(-1.0, T1, "ja", Lhoo, "Pji", 1.0, Lhvo, "Pai");
+  Tensor* hhoo = T("hhoo", {SO, SO}, 1);
+  e.axpy(1.0, c->hoo, "ij", 0.0, hhoo, "ij");
+  e.contract(1.0, c->hov, "ia", T1, "ja", 1.0, hhoo, "ij");
+  Tensor* hhvv = T("hhvv", {SV, SV}, 1);
+  e.axpy(1.0, c->hvv, "ab", 0.0, hhvv, "ab");
+  e.contract(-1.0, T1, "ia", c->hov, "ib", 1.0, hhvv, "ab");
+  Tensor* hhvo = T("hhvo", {SV, SO}, 1);
+  e.axpy(1.0, c->hvo, "ai", 0.0, hhvo, "ai");
+  e.contract(1.0, c->hvv, "ab", T1, "ib", 1.0, hhvo, "ai");
+  e.contract(-1.0, T1, "ja", hhoo, "ji", 1.0, hhvo, "ai");
+
+  // dressed Fock matrix F = hhat + 2 Lhat J - Lhat_pk Lhat_kq
+  Tensor* J = T("J", {SQ}, 1);
+  e.contract(1.0, Lhoo, "Pkl", c->Ioo, "kl", 0.0, J, "P");
+  Tensor* Foo = T("Foo", {SO, SO}, 1);
+  e.axpy(1.0, hhoo, "ij", 0.0, Foo, "ij");
+  e.contract(2.0, Lhoo, "Pij", J, "P", 1.0, Foo, "ij");
+  e.contract(-1.0, Lhoo, "Pik", Lhoo, "Pkj", 1.0, Foo, "ij");
+  Tensor* Fov = T("Fov", {SO, SV}, 1);
+  e.axpy(1.0, c->hov, "ia", 0.0, Fov, "ia");
+  e.contract(2.0, Lov, "Pia", J, "P", 1.0, Fov, "ia");
+  e.contract(-1.0, Lhoo, "Pik", Lov, "Pka", 1.0, Fov, "ia");
+  Tensor* Fvo = T("Fvo", {SV, SO}, 1);
+  e.axpy(1.0, hhvo, "ai", 0.0, Fvo, "ai");
+  e.contract(2.0, Lhvo, "Pai", J, "P", 1.0, Fvo, "ai");
+  e.contract(-1.0, Lhvo, "Pak", Lhoo, "Pki", 1.0, Fvo, "ai");
+  Tensor* Fvv = T("Fvv", {SV, SV}, 1);
+  e.axpy(1.0, hhvv, "ab", 0.0, Fvv, "ab");
+  e.contract(2.0, Lhvv, "Pab", J, "P", 1.0, Fvv, "ab");
+  e.contract(-1.0, Lhvo, "Pak", Lov, "Pkb", 1.0, Fvv, "ab");
+
+  // Cholesky-built integrals (Eq. 1), Mulliken order
+  Tensor* Govov = T("Govov", {SO, SV, SO, SV}, 2);
+  e.contract(1.0, Lov, "Pia", Lov, "Pjb", 0.0, Govov, "iajb");
+  Tensor* Gvovo = T("Gvovo", {SV, SO, SV, SO}, 2);
+  e.contract(1.0, Lhvo, "Pai", Lhvo, "Pbj", 0.0, Gvovo, "aibj");
+  Tensor* Goooo = T("Goooo", {SO, SO, SO, SO}, 2);
+  e.contract(1.0, Lhoo, "Pki", Lhoo, "Plj", 0.0, Goooo, "kilj");
+  Tensor* Goovv = T("Goovv", {SO, SO, SV, SV}, 2);
+  e.contract(1.0, Lhoo, "Pki", Lhvv, "Pac", 0.0, Goovv, "kiac");
+  Tensor* Govvo = T("Govvo", {SO, SV, SV, SO}, 2);
+  e.contract(1.0, Lov, "Pme", Lhvo, "Pbj", 0.0, Govvo, "mebj");
+  // particle-particle ladder integrals (ac|bd), built from Lhat_vv
+  Tensor* Wvvvv = T("Wvvvv", {SV, SV, SV, SV}, 2);
+  e.contract(1.0, Lhvv, "Pac", Lhvv, "Pbd", 0.0, Wvvvv, "acbd");
+
+  Tensor* u = T("u", {SO, SO, SV, SV}, 2);
+  e.axpy(2.0, t2s, "ijab", 0.0, u, "ijab");
+  e.axpy(-1.0, t2s, "ijba", 1.0, u, "ijab");
+
+  // ---- singles
+  Tensor* R1 = c->R1;
+  e.axpy(1.0, Fvo, "ai", 0.0, R1, "ia");
+  Tensor* Yt = T("Yt", {SQ, SO, SV}, 1);
+  e.contract(1.0, u, "kicd", Lov, "Pkc", 0.0, Yt, "Pid");
+  e.contract(1.0, Lhvv, "Pad", Yt, "Pid", 1.0, R1, "ia");
+  Tensor* Zt = T("Zt", {SQ, SO, SV}, 1);
+  e.contract(1.0, u, "klac", Lov, "Plc", 0.0, Zt, "Pka");
+  e.contract(-1.0, Lhoo, "Pki", Zt, "Pka", 1.0, R1, "ia");
+  e.contract(1.0, u, "ikac", Fov, "kc", 1.0, R1, "ia");
+
+  // ---- doubles
+  Tensor* Rr = T("R2raw", {SO, SO, SV, SV}, 2);
+  e.axpy(1.0, Gvovo, "aibj", 0.0, Rr, "ijab");
+  e.contract(1.0, t2s, "ijcd", Wvvvv, "acbd", 1.0, Rr, "ijab");  // PPL
+  Tensor* Wh = T("Whh", {SO, SO, SO, SO}, 2);
+  e.axpy(1.0, Goooo, "kilj", 0.0, Wh, "kilj");
+  e.contract(1.0, t2s, "ijcd", Govov, "kcld", 1.0, Wh, "kilj");
+  e.contract(1.0, t2s, "klab", Wh, "kilj", 1.0, Rr, "ijab");     // hole-hole
+  // rings: spin-integrated P(ij)P(ab) t_im^ae W_mbej, direct (WA) and
+  // exchange (WC) spin patterns
+  Tensor* WA = T("WA", {SO, SV, SV, SO}, 2);
+  e.axpy(1.0, Govvo, "mebj", 0.0, WA, "mbej");
+  e.contract(0.5, u, "jnbf", Govov, "menf", 1.0, WA, "mbej");
+  e.contract(-0.5, t2s, "jnbf", Govov, "mfne", 1.0, WA, "mbej");
+  Tensor* WC = T("WC", {SO, SV, SV, SO}, 2);
+  e.axpy(-1.0, Goovv, "mjbe", 0.0, WC, "mbej");
+  e.contract(0.5, t2s, "jnfb", Govov, "mfne", 1.0, WC, "mbej");
+  Tensor* Rg = T("Ring", {SO, SO, SV, SV}, 2);
+  e.contract(1.0, WA, "mbej", u, "imae", 0.0, Rg, "ijab");
+  e.contract(1.0, WC, "mbej", t2s, "imae", 1.0, Rg, "ijab");
+  e.contract(1.0, WC, "mbei", t2s, "mjae", 1.0, Rg, "ijab");
+  e.axpy(1.0, Rg, "ijab", 1.0, Rr, "ijab");
+  e.axpy(1.0, Rg, "jiba", 1.0, Rr, "ijab");
+  // Fock-like terms
+  Tensor* Fvv2 = T("Fvv2", {SV, SV}, 1);
+  e.axpy(1.0, Fvv, "bc", 0.0, Fvv2, "bc");
+  e.contract(-1.0, u, "klbd", Govov, "ldkc", 1.0, Fvv2, "bc");
+  Tensor* Foo2 = T("Foo2", {SO, SO}, 1);
+  e.axpy(1.0, Foo, "kj", 0.0, Foo2, "kj");
+  e.contract(1.0, u, "ljcd", Govov, "kdlc", 1.0, Foo2, "kj");
+  Tensor* E1 = T("E1", {SO, SO, SV, SV}, 2);
+  e.contract(1.0, t2s, "ijac", Fvv2, "bc", 0.0, E1, "ijab");
+  e.contract(-1.0, t2s, "ikab", Foo2, "kj", 1.0, E1, "ijab");
+  e.axpy(1.0, E1, "ijab", 1.0, Rr, "ijab");
+  e.axpy(1.0, E1, "jiba", 1.0, Rr, "ijab");
+  // symmetrise
+  e.axpy(0.5, Rr, "ijab", 0.0, c->R2, "ijab");
+  e.axpy(0.5, Rr, "jiba", 1.0, c->R2, "ijab");
+
+  // ---- energy <0|Hhat|0> + sum (2(ia|jb) - (ib|ja)) t_ij^ab
+  Tensor* E = c->E;
+  e.contract(1.0, hhoo, "kl", c->Ioo, "kl", 0.0, E, "");
+  e.contract(1.0, Foo, "kl", c->Ioo, "kl", 1.0, E, "");
+  Tensor* Xe = T("Xe", {SO, SV, SO, SV}, 2);
+  e.axpy(2.0, Govov, "iajb", 0.0, Xe, "iajb");
+  e.axpy(-1.0, Govov, "ibja", 1.0, Xe, "iajb");
+  e.contract(1.0, Xe, "iajb", t2s, "ijab", 1.0, E, "");
+}
+
+double scalar(cdcc_ctx* c, const Tensor* t) {
+  double v = 0;
+  CK(cudaMemcpyAsync(&v, t->d, 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return v;
+}
+
+// err = R / D over the amplitude vector layout; returns max |R/D|
+double probe_step(cdcc_ctx* c, Tensor* R1, Tensor* R2, Tensor* e1) {
+  Engine& e = *c->eng;
+  CK(cudaMemsetAsync(c->d_max, 0, 8, c->st));
+  const DevTasks& t1 = e.update_tasks(c->T1->lay);
+  const DevTasks& t2 = e.update_tasks(c->T2->lay);
+  const int64_t n1 = c->T1->lay.size;
+  e.launches += jacobi_update(t1.tasks, t1.chunks, t1.nchunk, R1->d, nullptr,
+                              e1->d, c->d_eps, c->d_max, c->st);
+  e.launches += jacobi_update(t2.tasks, t2.chunks, t2.nchunk, R2->d, nullptr,
+                              e1->d + n1, c->d_eps, c->d_max, c->st);
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, c->d_max, 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  double v;
+  std::memcpy(&v, &bits, 8);
+  return v;
+}
+
+void diis_init(cdcc_ctx* c, Diis& D, const std::string& tag, int64_t n) {
+  D.dim = std::max(0, std::min(c->opt.diis_dim, 15));
+  D.count = D.next = 0;
+  D.n = n;
+  D.x.clear();
+  D.e.clear();
+  D.B.assign((size_t)D.dim * D.dim, 0.0);
+  for (int k = 0; k < D.dim; ++k) {
+    D.x.push_back(c->eng->flat(tag + "_x" + std::to_string(k), n));
+    D.e.push_back(c->eng->flat(tag + "_e" + std::to_string(k), n));
+  }
+}
+
+// Push (x, err) and overwrite x with the DIIS extrapolation.
+void diis_step(cdcc_ctx* c, Diis& D, Tensor* x, Tensor* err) {
+  if (D.dim < 2) return;
+  Engine& e = *c->eng;
+  const int s = D.next;
+  CK(cudaMemcpyAsync(D.x[s]->d, x->d, (size_t)D.n * 8,
+                     cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(D.e[s]->d, err->d, (size_t)D.n * 8,
+                     cudaMemcpyDeviceToDevice, c->st));
+  D.next = (D.next + 1) % D.dim;
+  D.count = std::min(D.count + 1, D.dim);
+  const int m = D.count;
+  std::vector<const double*> xs(m);
+  for (int k = 0; k < m; ++k) xs[k] = D.e[k]->d;
+  e.launches += multi_dot(xs.data(), m, D.e[s]->d, D.n, c->d_partial,
+                          c->d_dots, c->st);
+  std::vector<double> dots(m);
+  CK(cudaMemcpyAsync(dots.data(), c->d_dots, m * 8, cudaMemcpyDeviceToHost,
+                     c->st));
+  CK(cudaStreamSynchronize(c->st));
+  for (int k = 0; k < m; ++k) {
+    D.B[s * D.dim + k] = dots[k];
+    D.B[k * D.dim + s] = dots[k];
+  }
+  if (m < 2) return;
+  // solve [B -1; -1 0][c; l] = [0; -1] (scaled), Gaussian elimination
+  const int N = m + 1;
+  std::vector<double> A((size_t)N * N, 0.0), rhs(N, 0.0);
+  double sc = 0;
+  for (int i = 0; i < m; ++i) sc = std::max(sc, D.B[i * D.dim + i]);
+  if (!(sc > 0)) sc = 1;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) A[i * N + j] = D.B[i * D.dim + j] / sc;
+  for (int i = 0; i < m; ++i) {
+    A[i * N + m] = -1.0;
+    A[m * N + i] = -1.0;
+  }
+  rhs[m] = -1.0;
+  std::vector<int> piv(N);
+  for (int k = 0; k < N; ++k) {
+    int p = k;
+    for (int i = k + 1; i < N; ++i)
+      if (std::fabs(A[i * N + k]) > std::fabs(A[p * N + k])) p = i;
+    if (A[p * N + k] == 0.0) return;  // singular: skip extrapolation
+    if (p != k) {
+      for (int j = 0; j < N; ++j) std::swap(A[k * N + j], A[p * N + j]);
+      std::swap(rhs[k], rhs[p]);
+    }
+    for (int i = k + 1; i < N; ++i) {
+      const double f = A[i * N + k] / A[k * N + k];
+      for (int j = k; j < N; ++j) A[i * N + j] -= f * A[k * N + j];
+      rhs[i] -= f * rhs[k];
+    }
+  }
+  std::vector<double> sol(N);
+  for (int i = N - 1; i >= 0; --i) {
+    double v = rhs[i];
+    for (int j = i + 1; j < N; ++j) v -= A[i * N + j] * sol[j];
+    sol[i] = v / A[i * N + i];
+  }
+  std::vector<const double*> px(m);
+  for (int k = 0; k < m; ++k) px[k] = D.x[k]->d;
+  e.launches += lincomb(x->d, px.data(), sol.data(), m, D.n, c->st);
+}
+
+struct PhaseTimer {
+  cdcc_ctx* c;
+  int idx;
+  PhaseTimer(cdcc_ctx* c_, int i) : c(c_), idx(i) {
+    CK(cudaEventRecord(c->ev0, c->st));
+  }
+  void stop() {
+    CK(cudaEventRecord(c->ev1, c->st));
+    CK(cudaEventSynchronize(c->ev1));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    c->phase[idx] = ms * 1e-3;
+  }
+};
+
+void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
+  Engine& e = *c->eng;
+  PhaseTimer pt(c, 0);
+  e.zero(c->amp);
+  c->tape_ready = false;
+  diis_init(c, c->cc_diis, "ccdiis", c->amp->lay.size);
+  double e_old = 0, rmax = 0, E = 0;
+  bool have_old = false;
+  int it = 1;
+  for (; it <= c->opt.max_iter; ++it) {
+    residual(c);
+    E = scalar(c, c->E);
+    rmax = probe_step(c, c->R1, c->R2, c->err1);
+    if (!std::isfinite(rmax) || !std::isfinite(E))
+      throw StatusError(CDCC_ENUMERIC, "non-finite CCSD residual");
+    if (rmax <= c->opt.conv_tol && have_old &&
+        std::fabs(E - e_old) <= c->opt.energy_tol)
+      break;
+    e_old = E;
+    have_old = true;
+    e.launches += axpby(1.0, c->err1->d, 1.0, c->amp->d, c->amp->lay.size,
+                        c->st);
+    if (it >= 2) diis_step(c, c->cc_diis, c->amp, c->err1);
+  }
+  pt.stop();
+  if (it > c->opt.max_iter)
+    throw StatusError(CDCC_ENOCONV, "CCSD did not converge");
+  c->e_corr = E - c->e_ref;
+  if (e_corr) *e_corr = c->e_corr;
+  if (iters) *iters = it;
+  if (resid) *resid = rmax;
+  c->state = 2;
+}
+
+void ensure_tape(cdcc_ctx* c) {
+  if (c->tape_ready) return;
+  c->eng->clear_tape();
+  c->eng->record(true);
+  residual(c);
+  c->eng->record(false);
+  c->tape_ready = true;
+}
+
+void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
+  Engine& e = *c->eng;
+  PhaseTimer pt(c, 1);
+  ensure_tape(c);
+  e.zero(c->lam);
+  diis_init(c, c->lam_diis, "lamdiis", c->lam->lay.size);
+  Tensor* g = e.adjoint(c->amp);
+  Tensor* g1 = e.adjoint(c->T1);
+  Tensor* g2 = e.adjoint(c->T2);
+  double rmax = 0;
+  int it = 1;
+  for (; it <= c->opt.max_iter; ++it) {
+    e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}}, TAG_AMP);
+    rmax = probe_step(c, g1, g2, c->err1);
+    if (!std::isfinite(rmax))
+      throw StatusError(CDCC_ENUMERIC, "non-finite Lambda residual");
+    if (rmax <= c->opt.conv_tol) break;
+    e.launches += axpby(1.0, c->err1->d, 1.0, c->lam->d, c->lam->lay.size,
+                        c->st);
+    if (it >= 2) diis_step(c, c->lam_diis, c->lam, c->err1);
+  }
+  (void)g;
+  pt.stop();
+  if (it > c->opt.max_iter)
+    throw StatusError(CDCC_ENOCONV, "Lambda did not converge");
+  if (iters) *iters = it;
+  if (resid) *resid = rmax;
+  c->state = 3;
+}
+
+void run_density(cdcc_ctx* c, double* D1) {
+  Engine& e = *c->eng;
+  PhaseTimer pt(c, 2);
+  ensure_tape(c);
+  e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}},
+             TAG_L | TAG_H);
+  // Gamma^P_pq: embed the block adjoints into the packed pattern, symmetrise
+  e.zero(c->Gam);
+  e.axpy(1.0, e.adjoint(c->Loo), "Pij", 1.0, c->Gam, "Pij");
+  e.axpy(1.0, e.adjoint(c->Lov), "Pia", 1.0, c->Gam, "Pia");
+  e.axpy(1.0, e.adjoint(c->Lvo), "Pai", 1.0, c->Gam, "Pai");
+  e.axpy(1.0, e.adjoint(c->Lvv), "Pab", 1.0, c->Gam, "Pab");
+  e.axpy(0.5, c->Gam, "Ppq", 0.0, c->Gsym, "Ppq");
+  e.axpy(0.5, c->Gam, "Pqp", 1.0, c->Gsym, "Ppq");
+  // one-particle density
+  e.zero(c->D1a);
+  e.axpy(1.0, e.adjoint(c->hoo), "ij", 1.0, c->D1a, "ij");
+  e.axpy(1.0, e.adjoint(c->hov), "ia", 1.0, c->D1a, "ia");
+  e.axpy(1.0, e.adjoint(c->hvo), "ai", 1.0, c->D1a, "ai");
+  e.axpy(1.0, e.adjoint(c->hvv), "ab", 1.0, c->D1a, "ab");
+  e.axpy(0.5, c->D1a, "pq", 0.0, c->D1s, "pq");
+  e.axpy(0.5, c->D1a, "qp", 1.0, c->D1s, "pq");
+  pt.stop();
+  if (D1) {
+    const int n = c->hd.n;
+    std::vector<double> h = to_host(c, c->D1s);
+    std::vector<double> dense((size_t)n * n, 0.0);
+    visit_dense(c->D1s->lay, c->dims,
+                [&](int64_t off, int64_t di) { dense[di] = h[off]; });
+    std::memcpy(D1, dense.data(), dense.size() * 8);
+  }
+  c->state = 4;
+}
+
+size_t packed_size_g(const cdcc_ctx* c, int gx) {
+  size_t s = 0;
+  for (int gP = 0; gP < c->hd.h; ++gP) {
+    size_t pairs = 0;
+    for (int gp = 0; gp < c->hd.h; ++gp)
+      pairs += (size_t)c->dims.n[SA][gp] * c->dims.n[SA][gp ^ gP ^ gx];
+    s += (size_t)c->dims.n[SQ][gP] * pairs;
+  }
+  return s;
+}
+
+void run_contract(cdcc_ctx* c, int nx, const int32_t* x_irrep,
+                  const double* dL, double* g) {
+  Engine& e = *c->eng;
+  PhaseTimer pt(c, 3);
+  const int64_t nnz = c->Gsym->lay.size;
+  const bool dev = is_device_ptr(dL);
+  std::vector<double> out(nx, 0.0);
+  // group consecutive totally symmetric displacements
+  const int XB = 8;
+  double* stage = nullptr;
+  if (!dev) stage = e.scratch((int64_t)XB * nnz);
+  double* d_g = e.scratch(std::max(nx, 1));
+  const int64_t need = batched_dot_partial_doubles(nnz, XB);
+  double* part = e.scratch(need);
+  std::vector<double> gtmp(XB);
+  int64_t off = 0;
+  int x = 0;
+  while (x < nx) {
+    const int gx = x_irrep ? x_irrep[x] : 0;
+    if (gx < 0 || gx >= c->hd.h)
+      throw StatusError(CDCC_EINVAL, "displacement irrep out of range");
+    if (gx != 0) {
+      off += (int64_t)packed_size_g(c, gx);
+      out[x++] = 0.0;
+      continue;
+    }
+    int cnt = 0;
+    while (x + cnt < nx && cnt < XB && (x_irrep ? x_irrep[x + cnt] : 0) == 0)
+      ++cnt;
+    const double* src = dL + off;
+    if (!dev) {
+      CK(cudaMemcpyAsync(stage, src, (size_t)cnt * nnz * 8,
+                         cudaMemcpyHostToDevice, c->st));
+      src = stage;
+    }
+    e.launches += batched_dot(c->Gsym->d, src, cnt, nnz, part, d_g, c->st);
+    CK(cudaMemcpyAsync(gtmp.data(), d_g, cnt * 8, cudaMemcpyDeviceToHost,
+                       c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int k = 0; k < cnt; ++k) out[x + k] = gtmp[k];
+    off += (int64_t)cnt * nnz;
+    x += cnt;
+  }
+  e.release_scratch();
+  pt.stop();
+  std::memcpy(g, out.data(), nx * 8);
+}
+
+void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
+              const int32_t* orb_irrep, const double* eps,
+              const int32_t* chol_irrep, const double* L) {
+  if (!(nirrep == 1 || nirrep == 2 || nirrep == 4 || nirrep == 8))
+    throw StatusError(CDCC_EINVAL, "nirrep must be 1, 2, 4 or 8");
+  if (nocc < 1 || nvir < 1 || nchol < 1)
+    throw StatusError(CDCC_EINVAL, "nocc, nvir, nchol must be >= 1");
+  if (!orb_irrep || !eps || !chol_irrep || !L)
+    throw StatusError(CDCC_EINVAL, "null input pointer");
+  const int n = nocc + nvir;
+  c->hd = {nirrep, nocc, nvir, n, nchol};
+  c->orb_irrep.assign(orb_irrep, orb_irrep + n);
+  c->chol_irrep.assign(chol_irrep, chol_irrep + nchol);
+  c->eps.assign(eps, eps + n);
+  Dims& d = c->dims;
+  d.h = nirrep;
+  for (int p = 0; p < n; ++p) {
+    const int g = orb_irrep[p];
+    if (g < 0 || g >= nirrep)
+      throw StatusError(CDCC_EINVAL, "orbital irrep out of range");
+    if (p > 0 && p != nocc && orb_irrep[p - 1] > g)
+      throw StatusError(CDCC_EINVAL,
+                        "orbitals must be sorted by irrep within occ / vir");
+    d.n[p < nocc ? SO : SV][g]++;
+  }
+  for (int P = 0; P < nchol; ++P) {
+    const int g = chol_irrep[P];
+    if (g < 0 || g >= nirrep)
+      throw StatusError(CDCC_EINVAL, "Cholesky irrep out of range");
+    if (P > 0 && chol_irrep[P - 1] > g)
+      throw StatusError(CDCC_EINVAL, "Cholesky vectors must be sorted");
+    d.n[SQ][g]++;
+  }
+  double emax_o = -1e300, emin_v = 1e300;
+  for (int p = 0; p < n; ++p) {
+    if (!std::isfinite(eps[p]))
+      throw StatusError(CDCC_EINVAL, "non-finite orbital energy");
+    if (p < nocc)
+      emax_o = std::max(emax_o, eps[p]);
+    else
+      emin_v = std::min(emin_v, eps[p]);
+  }
+  if (!(emax_o < emin_v))
+    throw StatusError(CDCC_EINVAL, "occupied and virtual energies overlap");
+  int so = 0, sv = 0, sq = 0;
+  for (int g = 0; g < nirrep; ++g) {
+    d.n[SA][g] = d.n[SO][g] + d.n[SV][g];
+    d.off_all[SO][g] = 0;
+    d.off_all[SV][g] = d.n[SO][g];
+    d.gstart[SO][g] = so;
+    d.gstart[SV][g] = sv;
+    d.gstart[SQ][g] = sq;
+    so += d.n[SO][g];
+    sv += d.n[SV][g];
+    sq += d.n[SQ][g];
+  }
+
+  CK(cudaSetDevice(c->opt.device));
+  c->st = (cudaStream_t)c->opt.stream;
+  DevAlloc al;
+  al.fa = c->opt.dev_alloc;
+  al.ff = c->opt.dev_free;
+  al.user = c->opt.alloc_user;
+  c->eng = std::make_unique<Engine>(d, c->st, al);
+  Engine& e = *c->eng;
+  CK(cudaEventCreate(&c->ev0));
+  CK(cudaEventCreate(&c->ev1));
+
+  c->Lpk = e.tensor("Lpk", {SQ, SA, SA}, 1);
+  c->nnz0 = c->Lpk->lay.size;
+  if ((size_t)c->nnz0 != packed_size_g(c, 0))
+    throw StatusError(CDCC_EINVAL, "internal: packed size mismatch");
+  if (!is_device_ptr(L)) {
+    // symmetry L^P_pq = L^P_qp inside the stored pattern
+    std::vector<double> dense;
+    const Layout& lay = c->Lpk->lay;
+    double maxasym = 0;
+    for (int gP = 0; gP < nirrep; ++gP) {
+      const int64_t base = lay.blk_off[gP];
+      const int64_t ncol = lay.ncol[gP];
+      for (int64_t k = 0; k < lay.nrow[gP]; ++k) {
+        const double* row = L + base + k * ncol;
+        int64_t coff = 0;
+        std::vector<int64_t> offs(nirrep);
+        for (int gp = 0; gp < nirrep; ++gp) {
+          offs[gp] = coff;
+          coff += (int64_t)d.n[SA][gp] * d.n[SA][gp ^ gP];
+        }
+        for (int gp = 0; gp < nirrep; ++gp) {
+          const int gq = gp ^ gP;
+          const int np_ = d.n[SA][gp], nq = d.n[SA][gq];
+          for (int p = 0; p < np_; ++p)
+            for (int q = 0; q < nq; ++q) {
+              const double a = row[offs[gp] + (int64_t)p * nq + q];
+              const double b = row[offs[gq] + (int64_t)q * np_ + p];
+              if (!std::isfinite(a))
+                throw StatusError(CDCC_EINVAL, "non-finite Cholesky vector");
+              maxasym = std::max(maxasym, std::fabs(a - b));
+            }
+        }
+      }
+    }
+    if (maxasym > 1e-12)
+      throw StatusError(CDCC_EINVAL, "L^P_pq is not symmetric in pq");
+  }
+  copy_in(c, c->Lpk->d, L, c->nnz0);
+  // blocks of L (leaves of the tape)
+  c->Loo = e.tensor("Loo", {SQ, SO, SO}, 1);
+  c->Lov = e.tensor("Lov", {SQ, SO, SV}, 1);
+  c->Lvo = e.tensor("Lvo", {SQ, SV, SO}, 1);
+  c->Lvv = e.tensor("Lvv", {SQ, SV, SV}, 1);
+  e.axpy(1.0, c->Lpk, "Ppq", 0.0, c->Loo, "Ppq");
+  e.axpy(1.0, c->Lpk, "Ppq", 0.0, c->Lov, "Ppq");
+  e.axpy(1.0, c->Lpk, "Ppq", 0.0, c->Lvo, "Ppq");
+  e.axpy(1.0, c->Lpk, "Ppq", 0.0, c->Lvv, "Ppq");
+  c->Loo->tag = c->Lov->tag = c->Lvo->tag = c->Lvv->tag = TAG_L;
+
+  // identity on the occupied space
+  c->Ioo = e.tensor("Ioo", {SO, SO}, 1);
+  {
+    std::vector<double> I((size_t)nocc * nocc, 0.0);
+    for (int i = 0; i < nocc; ++i) I[(size_t)i * nocc + i] = 1.0;
+    upload_dense(c, c->Ioo, I);
+  }
+  // core Hamiltonian h = diag(eps) - G(L), G = 2 L J - L_pk L_kq
+  c->hoo = e.tensor("hoo", {SO, SO}, 1);
+  c->hov = e.tensor("hov", {SO, SV}, 1);
+  c->hvo = e.tensor("hvo", {SV, SO}, 1);
+  c->hvv = e.tensor("hvv", {SV, SV}, 1);
+  {
+    std::vector<double> Eo((size_t)nocc * nocc, 0.0),
+        Ev((size_t)nvir * nvir, 0.0);
+    for (int i = 0; i < nocc; ++i) Eo[(size_t)i * nocc + i] = eps[i];
+    for (int a = 0; a < nvir; ++a) Ev[(size_t)a * nvir + a] = eps[nocc + a];
+    upload_dense(c, c->hoo, Eo);
+    upload_dense(c, c->hvv, Ev);
+    Tensor* J0 = e.tensor("J0", {SQ}, 1);
+    e.contract(1.0, c->Loo, "Pkl", c->Ioo, "kl", 0.0, J0, "P");
+    e.contract(-2.0, c->Loo, "Pij", J0, "P", 1.0, c->hoo, "ij");
+    e.contract(1.0, c->Loo, "Pik", c->Loo, "Pkj", 1.0, c->hoo, "ij");
+    e.contract(-2.0, c->Lov, "Pia", J0, "P", 0.0, c->hov, "ia");
+    e.contract(1.0, c->Loo, "Pik", c->Lov, "Pka", 1.0, c->hov, "ia");
+    e.contract(-2.0, c->Lvo, "Pai", J0, "P", 0.0, c->hvo, "ai");
+    e.contract(1.0, c->Lvo, "Pak", c->Loo, "Pki", 1.0, c->hvo, "ai");
+    e.contract(-2.0, c->Lvv, "Pab", J0, "P", 1.0, c->hvv, "ab");
+    e.contract(1.0, c->Lvo, "Pak", c->Lov, "Pkb", 1.0, c->hvv, "ab");
+  }
+  c->hoo->tag = c->hov->tag = c->hvo->tag = c->hvv->tag = TAG_H;
+  {
+    std::vector<double> h = to_host(c, c->hoo);
+    double tr = 0;
+    // trace over the diagonal blocks (rows == cols inside each irrep)
+    visit_dense(c->hoo->lay, c->dims, [&](int64_t off, int64_t di) {
+      if (di / nocc == di % nocc) tr += h[off];
+    });
+    double se = 0;
+    for (int i = 0; i < nocc; ++i) se += eps[i];
+    c->e_ref = tr + se;
+  }
+  // amplitude, residual and multiplier vectors [x1 | x2]
+  const Layout l1 = e.layout({SO, SV}, 1);
+  const Layout l2 = e.layout({SO, SO, SV, SV}, 2);
+  const int64_t na = l1.size + l2.size;
+  c->amp = e.flat("amp", na);
+  c->T1 = e.view("T1", c->amp, 0, {SO, SV}, 1);
+  c->T2 = e.view("T2", c->amp, l1.size, {SO, SO, SV, SV}, 2);
+  c->amp->tag = TAG_AMP;
+  c->T1->tag = c->T2->tag = TAG_AMP;
+  c->res = e.flat("res", na);
+  c->R1 = e.view("R1", c->res, 0, {SO, SV}, 1);
+  c->R2 = e.view("R2", c->res, l1.size, {SO, SO, SV, SV}, 2);
+  c->lam = e.flat("lam", na);
+  c->L1 = e.view("L1", c->lam, 0, {SO, SV}, 1);
+  c->L2 = e.view("L2", c->lam, l1.size, {SO, SO, SV, SV}, 2);
+  c->err1 = e.flat("err", na);
+  c->E = e.tensor("E", {}, 0);
+  c->Gam = e.tensor("Gam", {SQ, SA, SA}, 1);
+  c->Gsym = e.tensor("Gsym", {SQ, SA, SA}, 1);
+  c->D1a = e.tensor("D1a", {SA, SA}, 1);
+  c->D1s = e.tensor("D1s", {SA, SA}, 1);
+  // small device scalars
+  c->d_eps = (double*)e.al.alloc((size_t)n * 8);
+  CK(cudaMemcpyAsync(c->d_eps, eps, (size_t)n * 8, cudaMemcpyHostToDevice,
+                     c->st));
+  c->d_max = (unsigned long long*)e.al.alloc(8);
+  c->d_dots = (double*)e.al.alloc(16 * 8);
+  c->partial_n = multi_dot_partial_doubles(na, 16);
+  c->d_partial = (double*)e.al.alloc((size_t)c->partial_n * 8);
+  CK(cudaStreamSynchronize(c->st));
+  c->state = 1;
+}
+
+template <class F>
+cdcc_status guarded(cdcc_ctx* c, F f) {
+  try {
+    f();
+    return CDCC_OK;
+  } catch (const StatusError& s) {
+    if (c) c->err = s.m;
+    return s.s;
+  } catch (const EngineError& e) {
+    if (c) c->err = e.msg;
+    const std::string& m = e.msg;
+    if (m.find("alloc") != std::string::npos ||
+        m.find("out of memory") != std::string::npos)
+      return CDCC_ENOMEM;
+    if (m.rfind("CUDA", 0) == 0) return CDCC_ECUDA;
+    return CDCC_EINVAL;
+  } catch (const std::bad_alloc&) {
+    if (c) c->err = "host allocation failed";
+    return CDCC_ENOMEM;
+  } catch (const std::exception& e) {
+    if (c) c->err = e.what();
+    return CDCC_EINVAL;
+  }
+}
+
+void free_ctx(cdcc_ctx* c) {
+  if (!c) return;
+  if (c->eng) {
+    Engine& e = *c->eng;
+    e.al.release(c->d_eps, (size_t)c->hd.n * 8);
+    e.al.release(c->d_max, 8);
+    e.al.release(c->d_dots, 16 * 8);
+    e.al.release(c->d_partial, (size_t)c->partial_n * 8);
+    cudaStreamSynchronize(c->st);
+    c->eng.reset();
+  }
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  cudaStreamSynchronize(c->st);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cdcc_default_options(cdcc_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->conv_tol = 1e-10;
+  o->energy_tol = 1e-12;
+  o->max_iter = 100;
+  o->diis_dim = 8;
+  o->precision = CDCC_PREC_FP64;
+  o->switch_tol = 1e-6;
+  o->device = 0;
+  o->stream = nullptr;
+}
+
+cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
+                         int nchol, const int32_t* orb_irrep,
+                         const double* eps, const int32_t* chol_irrep,
+                         const double* L, const cdcc_options* opt) {
+  if (!out) return CDCC_EINVAL;
+  *out = nullptr;
+  cdcc_ctx* c = new (std::nothrow) cdcc_ctx();
+  if (!c) return CDCC_ENOMEM;
+  if (opt)
+    c->opt = *opt;
+  else
+    cdcc_default_options(&c->opt);
+  if (c->opt.max_iter <= 0) c->opt.max_iter = 100;
+  cdcc_status s = guarded(c, [&] {
+    init_ctx(c, nirrep, nocc, nvir, nchol, orb_irrep, eps, chol_irrep, L);
+  });
+  *out = c;  // also on error, so that cdcc_last_error can be read
+  return s;
+}
+
+size_t cdcc_packed_size(const cdcc_ctx* c, int gx) {
+  if (!c || c->state < 1 || gx < 0 || gx >= c->hd.h) return 0;
+  return packed_size_g(c, gx);
+}
+
+cdcc_status ccsd_solve(cdcc_ctx* c, double* e_corr, int* iters,
+                       double* resid) {
+  if (!c || c->state < 1) return CDCC_ESTATE;
+  return guarded(c, [&] { run_ccsd(c, e_corr, iters, resid); });
+}
+
+cdcc_status lambda_solve(cdcc_ctx* c, int* iters, double* resid) {
+  if (!c) return CDCC_EINVAL;
+  if (c->state < 2) {
+    c->err = "lambda_solve before ccsd_solve";
+    return CDCC_ESTATE;
+  }
+  return guarded(c, [&] { run_lambda(c, iters, resid); });
+}
+
+cdcc_status build_density(cdcc_ctx* c, double* D1) {
+  if (!c) return CDCC_EINVAL;
+  if (c->state < 3) {
+    c->err = "build_density before lambda_solve";
+    return CDCC_ESTATE;
+  }
+  return guarded(c, [&] { run_density(c, D1); });
+}
+
+cdcc_status cdcc_get_gamma(cdcc_ctx* c, double* gamma) {
+  if (!c || !gamma) return CDCC_EINVAL;
+  if (c->state < 4) return CDCC_ESTATE;
+  return guarded(c, [&] {
+    CK(cudaMemcpyAsync(gamma, c->Gsym->d, (size_t)c->nnz0 * 8,
+                       cudaMemcpyDefault, c->st));
+    CK(cudaStreamSynchronize(c->st));
+  });
+}
+
+cdcc_status contract_dL(cdcc_ctx* c, int nx, const int32_t* x_irrep,
+                        const double* dL, double* g) {
+  if (!c) return CDCC_EINVAL;
+  if (c->state < 4) {
+    c->err = "contract_dL before build_density";
+    return CDCC_ESTATE;
+  }
+  if (nx < 0 || (nx > 0 && (!dL || !g))) return CDCC_EINVAL;
+  if (nx == 0) return CDCC_OK;
+  return guarded(c, [&] { run_contract(c, nx, x_irrep, dL, g); });
+}
+
+cdcc_status gradient(cdcc_ctx* c, int nx, const int32_t* x_irrep,
+                     const double* dL, double* e_corr, double* g) {
+  if (!c || c->state < 1) return CDCC_ESTATE;
+  cdcc_status s = CDCC_OK;
+  if (c->state < 2) s = ccsd_solve(c, e_corr, nullptr, nullptr);
+  if (s != CDCC_OK) return s;
+  if (e_corr) *e_corr = c->e_corr;
+  if (c->state < 3) s = lambda_solve(c, nullptr, nullptr);
+  if (s != CDCC_OK) return s;
+  if (c->state < 4) s = build_density(c, nullptr);
+  if (s != CDCC_OK) return s;
+  return contract_dL(c, nx, x_irrep, dL, g);
+}
+
+cdcc_status cdcc_get_amplitudes(cdcc_ctx* c, int which, double* out) {
+  if (!c || !out || which < 0 || which > 3) return CDCC_EINVAL;
+  if ((which < 2 && c->state < 2) || (which >= 2 && c->state < 3))
+    return CDCC_ESTATE;
+  return guarded(c, [&] {
+    Tensor* t = which == 0 ? c->T1 : which == 1 ? c->T2
+              : which == 2 ? c->L1 : c->L2;
+    std::vector<double> h = to_host(c, t);
+    const int o = c->hd.nocc, v = c->hd.nvir;
+    const size_t n = which % 2 == 0 ? (size_t)o * v : (size_t)o * o * v * v;
+    std::memset(out, 0, n * 8);
+    visit_dense(t->lay, c->dims,
+                [&](int64_t off, int64_t di) { out[di] = h[off]; });
+  });
+}
+
+cdcc_status cdcc_phase_times(cdcc_ctx* c, double* t4) {
+  if (!c || !t4) return CDCC_EINVAL;
+  for (int i = 0; i < 4; ++i) t4[i] = c->phase[i];
+  return CDCC_OK;
+}
+
+long long cdcc_kernel_launches(const cdcc_ctx* c) {
+  return c && c->eng ? (long long)c->eng->launches : 0;
+}
+
+const char* cdcc_last_error(const cdcc_ctx* c) {
+  return c ? c->err.c_str() : "null context";
+}
+
+void cd_ccsd_free(cdcc_ctx* c) { free_ctx(c); }
+
+}  // extern "C"

@@ -1,0 +1,561 @@
+// engine.cu -- contraction planner, permutation tasks and reverse-mode tape.
+#include "engine.h"
+
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+
+namespace cdcc {
+
+#define ECK(x)                                                            \
+  do {                                                                    \
+    cudaError_t e_ = (x);                                                 \
+    if (e_ != cudaSuccess)                                                \
+      throw EngineError(std::string("CUDA: ") + cudaGetErrorString(e_) + \
+                        " at " #x);                                       \
+  } while (0)
+
+void* DevAlloc::alloc(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (fa) {
+    p = fa(bytes, (void*)st, user);
+    if (!p) throw EngineError("device allocation callback failed");
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      throw EngineError(std::string("cudaMallocAsync: ") +
+                        cudaGetErrorString(e));
+    }
+  }
+  return p;
+}
+
+void DevAlloc::release(void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 256;
+  if (ff)
+    ff(p, bytes, (void*)st, user);
+  else
+    cudaFreeAsync(p, st);
+}
+
+Engine::Engine(const Dims& d, cudaStream_t st, DevAlloc a)
+    : al(a), dims_(d), st_(st) {
+  al.st = st;
+}
+
+Engine::~Engine() {
+  for (auto& kv : tensors_) {
+    Tensor* t = kv.second.get();
+    if (t->owns && t->d) al.release(t->d, (size_t)t->lay.size * 8);
+  }
+  for (auto& kv : task_cache_) {
+    al.release(kv.second.tasks, kv.second.ntask * sizeof(PermTask));
+    al.release(kv.second.chunks, kv.second.nchunk * sizeof(Chunk));
+  }
+  for (auto& b : pool_) al.release(b.d, (size_t)b.n * 8);
+}
+
+Layout Engine::make_layout(const std::vector<int>& spaces, int split,
+                           int gtot) {
+  Layout L;
+  L.rank = (int)spaces.size();
+  if (L.rank > MAXRANK) throw EngineError("rank > 4");
+  for (int q = 0; q < L.rank; ++q) L.sp[q] = spaces[q];
+  L.split = split;
+  L.gtot = gtot;
+  L.build(dims_);
+  return L;
+}
+
+Tensor* Engine::new_tensor(const std::string& name, std::vector<int> spaces,
+                           int split, int gtot) {
+  auto t = std::make_unique<Tensor>();
+  t->name = name;
+  t->lay = make_layout(spaces, split, gtot);
+  t->d = (double*)al.alloc((size_t)std::max<int64_t>(t->lay.size, 1) * 8);
+  ECK(cudaMemsetAsync(t->d, 0, (size_t)std::max<int64_t>(t->lay.size, 1) * 8,
+                      st_));
+  Tensor* r = t.get();
+  tensors_[name] = std::move(t);
+  return r;
+}
+
+Tensor* Engine::tensor(const std::string& name, std::vector<int> spaces,
+                       int split, int gtot) {
+  auto it = tensors_.find(name);
+  if (it != tensors_.end()) {
+    Layout L = make_layout(spaces, split, gtot);
+    if (!L.same(it->second->lay))
+      throw EngineError("tensor '" + name + "' re-declared with new layout");
+    return it->second.get();
+  }
+  return new_tensor(name, spaces, split, gtot);
+}
+
+Tensor* Engine::flat(const std::string& name, int64_t n) {
+  auto it = tensors_.find(name);
+  if (it != tensors_.end()) {
+    if (it->second->lay.size != n)
+      throw EngineError("flat '" + name + "' re-declared with new size");
+    return it->second.get();
+  }
+  auto t = std::make_unique<Tensor>();
+  t->name = name;
+  t->lay.rank = -1;
+  t->lay.size = n;
+  t->d = (double*)al.alloc((size_t)std::max<int64_t>(n, 1) * 8);
+  ECK(cudaMemsetAsync(t->d, 0, (size_t)std::max<int64_t>(n, 1) * 8, st_));
+  Tensor* r = t.get();
+  tensors_[name] = std::move(t);
+  return r;
+}
+
+Tensor* Engine::view(const std::string& name, Tensor* parent, int64_t offset,
+                     std::vector<int> spaces, int split, int gtot) {
+  auto it = tensors_.find(name);
+  if (it != tensors_.end()) return it->second.get();
+  auto t = std::make_unique<Tensor>();
+  t->name = name;
+  t->lay = make_layout(spaces, split, gtot);
+  if (offset + t->lay.size > parent->lay.size)
+    throw EngineError("view '" + name + "' exceeds its parent");
+  t->d = parent->d + offset;
+  t->owns = false;
+  t->parent = parent;
+  t->offset = offset;
+  Tensor* r = t.get();
+  tensors_[name] = std::move(t);
+  return r;
+}
+
+Tensor* Engine::find(const std::string& name) {
+  auto it = tensors_.find(name);
+  return it == tensors_.end() ? nullptr : it->second.get();
+}
+
+Tensor* Engine::adjoint(Tensor* t) {
+  if (t->adj) return t->adj;
+  if (t->parent) {
+    Tensor* pa = adjoint(t->parent);
+    std::vector<int> sp(t->lay.sp, t->lay.sp + t->lay.rank);
+    t->adj = view(t->name + "~", pa, t->offset, sp, t->lay.split,
+                  t->lay.gtot);
+  } else if (t->lay.rank < 0) {
+    t->adj = flat(t->name + "~", t->lay.size);
+  } else {
+    std::vector<int> sp(t->lay.sp, t->lay.sp + t->lay.rank);
+    t->adj = tensor(t->name + "~", sp, t->lay.split, t->lay.gtot);
+  }
+  return t->adj;
+}
+
+void Engine::zero(Tensor* t) {
+  if (t->lay.size > 0)
+    ECK(cudaMemsetAsync(t->d, 0, (size_t)t->lay.size * 8, st_));
+}
+
+double* Engine::scratch(int64_t n) {
+  n = std::max<int64_t>(n, 1);
+  int best = -1;
+  for (int i = 0; i < (int)pool_.size(); ++i)
+    if (!pool_[i].busy && pool_[i].n >= n &&
+        (best < 0 || pool_[i].n < pool_[best].n))
+      best = i;
+  if (best < 0) {
+    Buf b;
+    b.n = n;
+    b.d = (double*)al.alloc((size_t)n * 8);
+    b.busy = false;
+    pool_.push_back(b);
+    best = (int)pool_.size() - 1;
+  }
+  pool_[best].busy = true;
+  return pool_[best].d;
+}
+
+void Engine::release_scratch() {
+  for (auto& b : pool_) b.busy = false;
+}
+
+const DevTasks& Engine::perm_tasks(const Layout& Y, const Layout& X,
+                                   const int* xq, bool eps) {
+  std::ostringstream key;
+  key << Y.key() << '<' << X.key() << ':';
+  for (int q = 0; q < Y.rank; ++q) key << xq[q];
+  if (eps) key << 'e';
+  auto it = task_cache_.find(key.str());
+  if (it != task_cache_.end()) return it->second;
+
+  const int nocc = dims_.total(SO);
+  std::vector<PermTask> tasks;
+  bool embed = false;
+  for_each_tuple(dims_.h, Y.rank, Y.gtot, [&](const int* gy) {
+    int gx[MAXRANK] = {0, 0, 0, 0};
+    for (int q = 0; q < Y.rank; ++q) gx[xq[q]] = gy[q];
+    SubBlock SY = sub_block(Y, dims_, gy);
+    SubBlock SX = sub_block(X, dims_, gx);
+    PermTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.rank = Y.rank;
+    t.ybase = SY.base;
+    t.xbase = SX.base;
+    int64_t n = 1;
+    for (int q = 0; q < Y.rank; ++q) {
+      const int ys = Y.sp[q], xs = X.sp[xq[q]], g = gy[q];
+      int dim;
+      if (ys == xs) {
+        dim = dims_.n[ys][g];
+      } else if (xs == SA && (ys == SO || ys == SV)) {
+        dim = dims_.n[ys][g];
+        t.xbase += (int64_t)dims_.off_all[ys][g] * SX.stride[xq[q]];
+      } else if (ys == SA && (xs == SO || xs == SV)) {
+        dim = dims_.n[xs][g];
+        t.ybase += (int64_t)dims_.off_all[xs][g] * SY.stride[q];
+        embed = true;
+      } else {
+        throw EngineError("axpy: incompatible index spaces");
+      }
+      t.dim[q] = dim;
+      t.ys[q] = SY.stride[q];
+      t.xs[q] = SX.stride[xq[q]];
+      if (eps) {
+        const int s = ys;
+        if (s == SO) {
+          t.gidx[q] = dims_.gstart[SO][g];
+          t.sgn[q] = 1;
+        } else if (s == SV) {
+          t.gidx[q] = nocc + dims_.gstart[SV][g];
+          t.sgn[q] = -1;
+        }
+      }
+      n *= dim;
+    }
+    t.n = n;
+    if (n > 0) {
+      // every access of the box must stay inside both buffers
+      int64_t ymax = t.ybase, xmax = t.xbase;
+      for (int q = 0; q < Y.rank; ++q) {
+        ymax += (int64_t)(t.dim[q] - 1) * t.ys[q];
+        xmax += (int64_t)(t.dim[q] - 1) * t.xs[q];
+      }
+      if (t.ybase < 0 || t.xbase < 0 || ymax >= Y.size || xmax >= X.size)
+        throw EngineError("internal: permutation task out of bounds");
+      tasks.push_back(t);
+    }
+  });
+  if (Y.rank == 0 && Y.gtot == 0 && tasks.empty()) {
+    // scalar copy
+    PermTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.n = 1;
+    tasks.push_back(t);
+  }
+  std::vector<Chunk> chunks;
+  const int CH = chunk_elems();
+  for (int i = 0; i < (int)tasks.size(); ++i)
+    for (int64_t s = 0; s < tasks[i].n; s += CH) chunks.push_back({i, s});
+  DevTasks dt;
+  dt.ntask = (int)tasks.size();
+  dt.nchunk = (int)chunks.size();
+  dt.embed = embed;
+  if (dt.ntask) {
+    dt.tasks = (PermTask*)al.alloc(tasks.size() * sizeof(PermTask));
+    dt.chunks = (Chunk*)al.alloc(chunks.size() * sizeof(Chunk));
+    ECK(cudaMemcpyAsync(dt.tasks, tasks.data(),
+                        tasks.size() * sizeof(PermTask),
+                        cudaMemcpyHostToDevice, st_));
+    ECK(cudaMemcpyAsync(dt.chunks, chunks.data(),
+                        chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice,
+                        st_));
+    ECK(cudaStreamSynchronize(st_));  // host vectors go out of scope
+  }
+  return task_cache_.emplace(key.str(), dt).first->second;
+}
+
+const DevTasks& Engine::update_tasks(const Layout& L) {
+  int xq[MAXRANK] = {0, 1, 2, 3};
+  return perm_tasks(L, L, xq, true);
+}
+
+void Engine::axpy_raw(double alpha, const Layout& XL, const double* X,
+                      const std::string& ix, double beta, const Layout& YL,
+                      double* Y, const std::string& iy) {
+  if ((int)ix.size() != XL.rank || (int)iy.size() != YL.rank ||
+      XL.rank != YL.rank)
+    throw EngineError("axpy: rank / index string mismatch " + ix + "->" + iy);
+  if (XL.gtot != YL.gtot) throw EngineError("axpy: symmetry mismatch");
+  int xq[MAXRANK] = {0, 0, 0, 0};
+  for (int q = 0; q < YL.rank; ++q) {
+    const size_t p = ix.find(iy[q]);
+    if (p == std::string::npos)
+      throw EngineError("axpy: index sets differ " + ix + "->" + iy);
+    xq[q] = (int)p;
+  }
+  const DevTasks& dt = perm_tasks(YL, XL, xq, false);
+  if (dt.embed && beta != 1.0)
+    throw EngineError("axpy: embedding requires beta = 1");
+  launches += perm_axpy(dt.tasks, dt.chunks, dt.nchunk, alpha, X, beta, Y,
+                        st_);
+}
+
+void Engine::axpy(double alpha, Tensor* X, const char* ix, double beta,
+                  Tensor* Y, const char* iy) {
+  if (recording_) tape_.push_back({1, alpha, beta, X, nullptr, Y, ix, "", iy});
+  axpy_raw(alpha, X->lay, X->d, ix, beta, Y->lay, Y->d, iy);
+}
+
+void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
+                      const char* ib_, double beta, Tensor* C,
+                      const char* ic_) {
+  const std::string ia(ia_), ib(ib_), ic(ic_);
+  if ((int)ia.size() != A->lay.rank || (int)ib.size() != B->lay.rank ||
+      (int)ic.size() != C->lay.rank)
+    throw EngineError("contract: index strings " + ia + "," + ib + "->" + ic +
+                      " do not match ranks");
+  if (recording_) tape_.push_back({0, alpha, beta, A, B, C, ia, ib, ic});
+
+  std::string KA, KB, fA_A, fB_B, fA_C, fB_C;
+  for (char x : ia) {
+    if (ic.find(x) != std::string::npos) {
+      if (ib.find(x) != std::string::npos)
+        throw EngineError("contract: batch index unsupported");
+      fA_A += x;
+    } else if (ib.find(x) != std::string::npos) {
+      KA += x;
+    } else {
+      throw EngineError("contract: index summed in one operand only");
+    }
+  }
+  for (char x : ib) {
+    if (ic.find(x) != std::string::npos)
+      fB_B += x;
+    else if (ia.find(x) != std::string::npos)
+      KB += x;
+    else
+      throw EngineError("contract: index summed in one operand only");
+  }
+  for (char x : ic) {
+    const bool a = ia.find(x) != std::string::npos;
+    const bool b = ib.find(x) != std::string::npos;
+    if (a == b) throw EngineError("contract: output index " +
+                                  std::string(1, x) + " ambiguous");
+    (a ? fA_C : fB_C) += x;
+  }
+  // letter -> space
+  auto space_of = [&](char x) -> int {
+    size_t p = ia.find(x);
+    if (p != std::string::npos) return A->lay.sp[p];
+    p = ib.find(x);
+    return B->lay.sp[p];
+  };
+  for (char x : ia) {
+    size_t p = ib.find(x);
+    if (p != std::string::npos && B->lay.sp[p] != A->lay.sp[ia.find(x)])
+      throw EngineError("contract: index space mismatch");
+  }
+
+  auto matches = [](const Tensor* T, const std::string& tl,
+                    const std::string& r, const std::string& c, bool& tr) {
+    if (tl == r + c && T->lay.split == (int)r.size()) {
+      tr = false;
+      return true;
+    }
+    if (tl == c + r && T->lay.split == (int)c.size()) {
+      tr = true;
+      return true;
+    }
+    return false;
+  };
+
+  // enumerate plans
+  struct Plan {
+    int form;
+    std::string K, X, Y;
+    int64_t cost;
+  } best{0, "", "", "", -1};
+  const std::string Ks[2] = {KA, KB};
+  const std::string FAs[2] = {fA_C, fA_A};
+  const std::string FBs[2] = {fB_C, fB_B};
+  for (int kk = 0; kk < 2; ++kk)
+    for (int fa = 0; fa < 2; ++fa)
+      for (int fb = 0; fb < 2; ++fb)
+        for (int form = 0; form < 2; ++form) {
+          const std::string& K = Ks[kk];
+          const std::string X = form ? FBs[fb] : FAs[fa];
+          const std::string Y = form ? FAs[fa] : FBs[fb];
+          Tensor* P = form ? B : A;
+          Tensor* Q = form ? A : B;
+          const std::string& pl = form ? ib : ia;
+          const std::string& ql = form ? ia : ib;
+          bool tr;
+          int64_t cost = 0;
+          if (!matches(P, pl, X, K, tr)) cost += P->lay.size;
+          if (!matches(Q, ql, K, Y, tr)) cost += Q->lay.size;
+          if (!(ic == X + Y && C->lay.split == (int)X.size()))
+            cost += 2 * C->lay.size;
+          if (best.cost < 0 || cost < best.cost) best = {form, K, X, Y, cost};
+        }
+
+  Tensor* P = best.form ? B : A;
+  Tensor* Q = best.form ? A : B;
+  const std::string& pl = best.form ? ib : ia;
+  const std::string& ql = best.form ? ia : ib;
+
+  auto get = [&](Tensor* T, const std::string& tl, const std::string& r,
+                 const std::string& c) -> Mat {
+    bool tr;
+    if (matches(T, tl, r, c, tr)) return {T->d, &T->lay, tr};
+    std::vector<int> sp;
+    for (char x : r + c) sp.push_back(space_of(x));
+    tmp_layouts_.push_back(std::make_unique<Layout>(
+        make_layout(sp, (int)r.size(), T->lay.gtot)));
+    const Layout* L = tmp_layouts_.back().get();
+    double* buf = scratch(L->size);
+    axpy_raw(1.0, T->lay, T->d, tl, 0.0, *L, buf, r + c);
+    return {buf, L, false};
+  };
+  Mat mp = get(P, pl, best.X, best.K);
+  Mat mq = get(Q, ql, best.K, best.Y);
+  const int gP = P->lay.gtot, gQ = Q->lay.gtot;
+  const bool direct =
+      (ic == best.X + best.Y && C->lay.split == (int)best.X.size());
+  const Layout* DL;
+  double* Dd;
+  if (direct) {
+    DL = &C->lay;
+    Dd = C->d;
+  } else {
+    std::vector<int> sp;
+    for (char x : best.X + best.Y) sp.push_back(space_of(x));
+    tmp_layouts_.push_back(std::make_unique<Layout>(
+        make_layout(sp, (int)best.X.size(), gP ^ gQ)));
+    DL = tmp_layouts_.back().get();
+    Dd = scratch(DL->size);
+  }
+  if ((gP ^ gQ) != C->lay.gtot)
+    throw EngineError("contract: output symmetry mismatch");
+
+  GemmProb probs[GEMM_MAXPROB];
+  int np = 0;
+  const int h = dims_.h;
+  for (int GX = 0; GX < h; ++GX) {
+    const int GK = GX ^ gP;
+    GemmProb g;
+    std::memset(&g, 0, sizeof(g));
+    int64_t M, K, K2, N;
+    if (!mp.trans) {
+      M = mp.lay->nrow[GX];
+      K = mp.lay->ncol[GX];
+      g.A = mp.d + mp.lay->blk_off[GX];
+      g.lda = (int)K;
+    } else {
+      M = mp.lay->ncol[GK];
+      K = mp.lay->nrow[GK];
+      g.A = mp.d + mp.lay->blk_off[GK];
+      g.lda = (int)M;
+      g.ta = 1;
+    }
+    if (!mq.trans) {
+      K2 = mq.lay->nrow[GK];
+      N = mq.lay->ncol[GK];
+      g.B = mq.d + mq.lay->blk_off[GK];
+      g.ldb = (int)N;
+    } else {
+      const int GY = GK ^ gQ;
+      N = mq.lay->nrow[GY];
+      K2 = mq.lay->ncol[GY];
+      g.B = mq.d + mq.lay->blk_off[GY];
+      g.ldb = (int)K2;
+      g.tb = 1;
+    }
+    const int64_t Md = DL->nrow[GX], Nd = DL->ncol[GX];
+    if (Md == 0 || Nd == 0) continue;
+    if (M != Md || N != Nd || K != K2) {
+      std::ostringstream os;
+      os << "contract: block shape mismatch " << ia << "," << ib << "->"
+         << ic << " G=" << GX << " M" << M << "/" << Md << " N" << N << "/"
+         << Nd << " K" << K << "/" << K2;
+      throw EngineError(os.str());
+    }
+    if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX)
+      throw EngineError("contract: block too large");
+    g.C = Dd + DL->blk_off[GX];
+    g.ldc = (int)Nd;
+    // operand extents inside their buffers (blocks are dense row-major)
+    {
+      const int64_t aoff = g.A - mp.d, boff = g.B - mq.d;
+      if (aoff + M * K > mp.lay->size || boff + K * N > mq.lay->size ||
+          DL->blk_off[GX] + M * N > DL->size)
+        throw EngineError("internal: GEMM block out of bounds");
+    }
+    g.M = (int)M;
+    g.N = (int)N;
+    g.K = (int)K;
+    flops += 2 * M * N * K;
+    probs[np++] = g;
+  }
+  const int64_t sk = gemm_scratch_doubles(probs, np);
+  double* skb = sk > 0 ? scratch(sk) : nullptr;
+  launches += gemm64_grouped(probs, np, alpha, direct ? beta : 0.0, skb, st_);
+  if (!direct)
+    axpy_raw(1.0, *DL, Dd, best.X + best.Y, beta, C->lay, C->d, ic);
+  release_scratch();
+  tmp_layouts_.clear();
+}
+
+void Engine::backward(const std::vector<std::pair<Tensor*, Tensor*>>& seeds,
+                      int active) {
+  const bool rec = recording_;
+  recording_ = false;
+  for (auto& kv : tensors_) kv.second->req = false;
+  for (auto& kv : tensors_) {
+    Tensor* t = kv.second.get();
+    if (t->tag & active) t->req = true;
+  }
+  for (const Op& op : tape_) {
+    if (op.A->req || (op.kind == 0 && op.B->req)) op.C->req = true;
+  }
+  // zero adjoints of everything that carries one
+  std::vector<Tensor*> req;
+  for (auto& kv : tensors_)
+    if (kv.second->req) req.push_back(kv.second.get());
+  for (Tensor* t : req) zero(adjoint(t));
+  for (auto& s : seeds) {
+    if (!s.first->req) continue;
+    Tensor* a = adjoint(s.first);
+    if (s.second) {
+      ECK(cudaMemcpyAsync(a->d, s.second->d, (size_t)a->lay.size * 8,
+                          cudaMemcpyDeviceToDevice, st_));
+    } else {
+      const double one = 1.0;
+      ECK(cudaMemcpyAsync(a->d, &one, 8, cudaMemcpyHostToDevice, st_));
+      ECK(cudaStreamSynchronize(st_));
+    }
+  }
+  for (auto it = tape_.rbegin(); it != tape_.rend(); ++it) {
+    const Op& op = *it;
+    if (!op.C->req) continue;
+    Tensor* Cb = op.C->adj;
+    if (op.kind == 0) {
+      if (op.A->req)
+        contract(op.alpha, Cb, op.ic.c_str(), op.B, op.ib.c_str(), 1.0,
+                 adjoint(op.A), op.ia.c_str());
+      if (op.B->req)
+        contract(op.alpha, op.A, op.ia.c_str(), Cb, op.ic.c_str(), 1.0,
+                 adjoint(op.B), op.ib.c_str());
+    } else {
+      if (op.A->req)
+        axpy(op.alpha, Cb, op.ic.c_str(), 1.0, adjoint(op.A), op.ia.c_str());
+    }
+    if (op.beta == 0.0)
+      zero(Cb);
+    else if (op.beta != 1.0)
+      launches += axpby(0.0, Cb->d, op.beta, Cb->d, Cb->lay.size, st_);
+  }
+  recording_ = rec;
+}
+
+}  // namespace cdcc

@@ -1,0 +1,151 @@
+// engine.h -- symmetry-blocked tensor engine with a reverse-mode tape.
+//
+// Tensors are persistent, named DPD arrays (dpd.h) in device memory.  Two
+// primitive operations are provided:
+//   contract:  C = beta*C + alpha * sum_K A * B   (binary contraction; the
+//              planner permutes operands into matrix form when needed and
+//              issues ONE grouped GEMM over all irrep blocks)
+//   axpy:      Y = beta*Y + alpha * perm(X)       (index permutation, also
+//              extraction of / embedding into the "all orbitals" space)
+// When recording, each call is appended to a tape; backward() replays the
+// tape in reverse with the adjoint rules of the two primitives.  The Lambda
+// equations (Sec. 2.3) are the adjoint of the amplitude residual with
+// respect to the amplitudes, and the Cholesky-basis density Gamma^P
+// (Sec. 2.4, 2.6) is its adjoint with respect to the Cholesky vectors.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "dpd.h"
+#include "kernels.h"
+
+namespace cdcc {
+
+struct DevAlloc {
+  void* (*fa)(size_t, void*, void*) = nullptr;
+  void (*ff)(void*, size_t, void*, void*) = nullptr;
+  void* user = nullptr;
+  cudaStream_t st = 0;
+  void* alloc(size_t bytes);
+  void release(void* p, size_t bytes);
+};
+
+enum LeafTag : int { TAG_NONE = 0, TAG_AMP = 1, TAG_L = 2, TAG_H = 4 };
+
+struct Tensor {
+  std::string name;
+  Layout lay;
+  double* d = nullptr;
+  bool owns = true;
+  Tensor* parent = nullptr;  // view into parent's buffer
+  int64_t offset = 0;
+  int tag = TAG_NONE;        // leaf tag (0 = not a leaf)
+  Tensor* adj = nullptr;
+  bool req = false;
+};
+
+struct DevTasks {
+  PermTask* tasks = nullptr;
+  Chunk* chunks = nullptr;
+  int ntask = 0, nchunk = 0;
+  bool embed = false;
+};
+
+class EngineError : public std::exception {
+ public:
+  explicit EngineError(std::string m) : msg(std::move(m)) {}
+  const char* what() const noexcept override { return msg.c_str(); }
+  std::string msg;
+};
+
+class Engine {
+ public:
+  Engine(const Dims& d, cudaStream_t st, DevAlloc al);
+  ~Engine();
+
+  const Dims& dims() const { return dims_; }
+  cudaStream_t stream() const { return st_; }
+
+  // get-or-create a persistent tensor
+  Tensor* tensor(const std::string& name, std::vector<int> spaces, int split,
+                 int gtot = 0);
+  // a view of `n` doubles into `parent` at `offset` with its own layout
+  Tensor* view(const std::string& name, Tensor* parent, int64_t offset,
+               std::vector<int> spaces, int split, int gtot = 0);
+  Tensor* flat(const std::string& name, int64_t n);  // 1-D helper buffer
+  Tensor* find(const std::string& name);
+  Layout layout(const std::vector<int>& spaces, int split, int gtot = 0) {
+    return make_layout(spaces, split, gtot);
+  }
+
+  void zero(Tensor* t);
+  void contract(double alpha, Tensor* A, const char* ia, Tensor* B,
+                const char* ib, double beta, Tensor* C, const char* ic);
+  void axpy(double alpha, Tensor* X, const char* ix, double beta, Tensor* Y,
+            const char* iy);
+
+  // tape
+  void record(bool on) { recording_ = on; }
+  void clear_tape() { tape_.clear(); }
+  size_t tape_size() const { return tape_.size(); }
+  // Run the tape backwards.  `seeds`: (tensor, seed values tensor or null =
+  // all ones for rank-0 tensors).  Leaves whose tag is in `active` receive
+  // adjoints (tensor->adj).
+  void backward(const std::vector<std::pair<Tensor*, Tensor*>>& seeds,
+                int active);
+  Tensor* adjoint(Tensor* t);
+
+  // elementwise helpers on DPD tensors
+  const DevTasks& update_tasks(const Layout& L);  // with orbital energies
+  double* scratch(int64_t n);                     // per-call temporary
+  void release_scratch();
+
+  int64_t launches = 0;
+  int64_t flops = 0;  // FP64 GEMM flops issued
+
+  DevAlloc al;
+
+ private:
+  struct Op {
+    int kind;  // 0 contract, 1 axpy
+    double alpha, beta;
+    Tensor *A, *B, *C;
+    std::string ia, ib, ic;
+  };
+  struct Mat {
+    double* d;
+    const Layout* lay;
+    bool trans;
+  };
+
+  Tensor* new_tensor(const std::string& name, std::vector<int> spaces,
+                     int split, int gtot);
+  const DevTasks& perm_tasks(const Layout& Y, const Layout& X,
+                             const int* xq, bool eps);
+  void axpy_raw(double alpha, const Layout& XL, const double* X,
+                const std::string& ix, double beta, const Layout& YL,
+                double* Y, const std::string& iy);
+  Layout make_layout(const std::vector<int>& spaces, int split, int gtot);
+
+  Dims dims_;
+  cudaStream_t st_;
+  bool recording_ = false;
+  std::vector<Op> tape_;
+  std::map<std::string, std::unique_ptr<Tensor>> tensors_;
+  std::map<std::string, DevTasks> task_cache_;
+  // scratch pool
+  struct Buf {
+    double* d;
+    int64_t n;
+    bool busy;
+  };
+  std::vector<Buf> pool_;
+  std::vector<std::unique_ptr<Layout>> tmp_layouts_;
+};
+
+}  // namespace cdcc

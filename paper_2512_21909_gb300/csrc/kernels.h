@@ -1,0 +1,63 @@
+// kernels.h -- launchers of the CUDA kernels of the CD-CCSD library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "dpd.h"
+
+namespace cdcc {
+
+constexpr int GEMM_MAXPROB = 16;
+
+// One matrix product C = beta*C + alpha*op(A)*op(B), all row-major.
+// op(A) is M x K (ta: A stored K x M), op(B) is K x N (tb: B stored N x K).
+struct GemmProb {
+  const double* A;
+  const double* B;
+  double* C;
+  int M, N, K;
+  int lda, ldb, ldc;
+  int ta, tb;
+};
+
+// Grouped launch of up to GEMM_MAXPROB independent products sharing
+// alpha/beta.  Returns the number of kernel launches issued.  `scratch` is
+// used for split-K partial sums of thin products; it must hold
+// gemm_scratch_doubles(...) doubles (may be null if that is 0).
+int64_t gemm_scratch_doubles(const GemmProb* p, int np);
+int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
+                   double* scratch, cudaStream_t st);
+
+// Y = beta*Y + alpha*X over the boxes described by tasks/chunks.
+int perm_axpy(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
+              double alpha, const double* X, double beta, double* Y,
+              cudaStream_t st);
+
+// Jacobi step over DPD boxes: s = R / D (D from orbital energies),
+// t += s, err = s, and atomically max |s| into *d_maxbits.
+int jacobi_update(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
+                  const double* R, double* t, double* err, const double* eps,
+                  unsigned long long* d_maxbits, cudaStream_t st);
+
+// out[k] = dot(xs[k], y) for k < m (m <= 16), deterministic two-pass.
+int multi_dot(const double* const* xs, int m, const double* y, int64_t n,
+              double* d_partial, double* d_out, cudaStream_t st);
+int64_t multi_dot_partial_doubles(int64_t n, int m);
+
+// out = sum_k c[k] * xs[k]  (m <= 16)
+int lincomb(double* out, const double* const* xs, const double* c, int m,
+            int64_t n, cudaStream_t st);
+
+// y = a*x + b*y elementwise over n doubles
+int axpby(double a, const double* x, double b, double* y, int64_t n,
+          cudaStream_t st);
+
+// g[x] = sum_e G[e] * dL[x*nnz + e] for x < nx; deterministic, uses
+// `partial` (batched_dot_partial_doubles(nnz, nx) doubles).
+int64_t batched_dot_partial_doubles(int64_t nnz, int nx);
+int batched_dot(const double* G, const double* dL, int nx, int64_t nnz,
+                double* partial, double* d_g, cudaStream_t st);
+
+int chunk_elems();
+
+}  // namespace cdcc

@@ -1,0 +1,63 @@
+"""Write oracle reference values for the full-size parity tests.
+
+Calls only `oracle/` (and the seeded generators in `synth/`).  For each
+workload it stores the FP64 oracle's correlation energy, iteration counts,
+the gradient g_x for every displacement and a seeded sample of Gamma^P,
+t2 and lambda2 elements (packed / dense indices with values).
+
+    python tests/golden/make_golden.py 1        # writes tests/golden/c1.json
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from synth import make_system, make_displacements, unpack_dense, pack_dense  # noqa
+from oracle import model, lagrangian  # noqa
+
+
+def golden(idx: int, nsample: int = 64):
+    s = make_system(idx)
+    o = s.nocc
+    L = torch.as_tensor(unpack_dense(s, s.L))
+    h = model.core_from_eps(torch.as_tensor(s.eps), L, o)
+    t0 = time.time()
+    r = lagrangian.run_all(h, L, o, tol=1e-11, e_tol=1e-13, verbose=True)
+    secs = time.time() - t0
+    dL = make_displacements(s)
+    G = pack_dense(s, r["G"].numpy())
+    g = dL @ G
+    rng = np.random.default_rng(1234 + idx)
+    gi = rng.choice(G.size, nsample, replace=False)
+    t2 = r["cc"]["t2"].numpy()
+    l2 = r["lam"]["l2"].numpy()
+    big = np.argsort(-np.abs(t2).reshape(-1))[:nsample]
+    return dict(
+        workload=s.name, cfg_index=idx, scale=s.scale, tol=1e-11,
+        e_corr=r["cc"]["E_corr"], e_ref=r["cc"]["E_ref"],
+        ccsd_iterations=r["cc"]["iterations"],
+        lambda_iterations=r["lam"]["iterations"], oracle_seconds=secs,
+        gradient=g.tolist(),
+        gamma_index=gi.tolist(), gamma_value=G[gi].tolist(),
+        t2_index=big.tolist(), t2_value=t2.reshape(-1)[big].tolist(),
+        l2_value=l2.reshape(-1)[big].tolist(),
+        D1_trace=float(np.trace(r["D"].numpy())),
+    )
+
+
+if __name__ == "__main__":
+    for a in sys.argv[1:]:
+        idx = int(a)
+        out = golden(idx)
+        path = os.path.join(HERE, f"c{idx}.json")
+        with open(path, "w") as f:
+            json.dump(out, f, indent=1)
+        print("wrote", path, "E_corr", out["e_corr"])

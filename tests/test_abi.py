@@ -1,0 +1,86 @@
+"""C-ABI library: it loads, exports every declared symbol, and its host-side
+input validation rejects bad inputs before touching a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2512_21909_gb300 import build as cbuild
+from paper_2512_21909_gb300 import cdcc
+from synth import random_system
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cbuild.build()
+    return cdcc.load()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\([^;{]*\)\s*;",
+                             src, flags=re.M):
+            if not m.group(0).lstrip().startswith("typedef"):
+                names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_all_declared_symbols_exported(lib):
+    names = declared_functions()
+    assert "cd_ccsd_init" in names and "contract_dL" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_default_options(lib):
+    o = cdcc.cdcc_default_options()
+    assert o.conv_tol == 1e-10 and o.max_iter == 100 and o.diis_dim == 8
+    assert o.precision == cdcc.PREC_FP64
+
+
+def _init(s, **kw):
+    args = dict(nirrep=s.nirrep, nocc=s.nocc, nvir=s.nvir, nchol=s.nchol,
+                orb_irrep=s.orb_irrep, eps=s.eps, chol_irrep=s.chol_irrep,
+                L=s.L)
+    args.update(kw)
+    return cdcc.cd_ccsd_init(**args, use_torch_memory=False)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nirrep=3),
+    dict(nocc=0),
+    dict(orb_irrep="unsorted"),
+    dict(chol_irrep="out_of_range"),
+    dict(eps="overlap"),
+])
+def test_invalid_inputs_rejected_on_host(lib, bad):
+    s = random_system([1, 1], [2, 2], [3, 3], seed=1)
+    kw = {}
+    for k, v in bad.items():
+        if v == "unsorted":
+            oi = s.orb_irrep.copy()
+            oi[s.nocc:] = oi[s.nocc:][::-1]
+            kw[k] = oi
+        elif v == "out_of_range":
+            ci = s.chol_irrep.copy()
+            ci[-1] = 7
+            kw[k] = ci
+        elif v == "overlap":
+            e = s.eps.copy()
+            e[0] = 5.0
+            kw[k] = e
+        else:
+            kw[k] = v
+    with pytest.raises(cdcc.CdccError) as ei:
+        _init(s, **kw)
+    assert ei.value.status == cdcc.CDCC_EINVAL
