@@ -167,6 +167,17 @@ cdcc_status cdcc_get_amplitudes(cdcc_ctx *ctx, int which, double *out);
  * phases (device time of the stream, CUDA events). */
 cdcc_status cdcc_phase_times(cdcc_ctx *ctx, double *t4);
 
+/* Per-kernel-class timing (CUDA events on the context's stream, around
+ * every launch of the class while enabled).  Classes:
+ *   0 FP64 GEMM (work = flops)          1 permutation / axpy (work = bytes)
+ *   2 amplitude update (work = bytes)   3 contract_dL batched dot (bytes)
+ *   4 other vector kernels (bytes)
+ * cdcc_kernel_stats returns the accumulated device seconds, launches and
+ * algorithmic work since the context was created. */
+cdcc_status cdcc_profile(cdcc_ctx *ctx, int enable);
+cdcc_status cdcc_kernel_stats(cdcc_ctx *ctx, int kind, double *seconds,
+                              long long *launches, double *work);
+
 /* Number of kernels this context has launched so far. */
 long long cdcc_kernel_launches(const cdcc_ctx *ctx);
 

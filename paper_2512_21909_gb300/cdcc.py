@@ -75,6 +75,11 @@ def load():
     L.gradient.argtypes = [vp, ctypes.c_int, vp, vp, P(ctypes.c_double), vp]
     L.cdcc_get_amplitudes.argtypes = [vp, ctypes.c_int, vp]
     L.cdcc_phase_times.argtypes = [vp, vp]
+    L.cdcc_profile.argtypes = [vp, ctypes.c_int]
+    L.cdcc_profile.restype = ctypes.c_int
+    L.cdcc_kernel_stats.argtypes = [vp, ctypes.c_int, P(ctypes.c_double),
+                                    P(ctypes.c_longlong), P(ctypes.c_double)]
+    L.cdcc_kernel_stats.restype = ctypes.c_int
     L.cdcc_kernel_launches.argtypes = [vp]
     L.cdcc_kernel_launches.restype = ctypes.c_longlong
     L.cdcc_last_error.argtypes = [vp]
@@ -283,6 +288,22 @@ def cdcc_phase_times(ctx):
     _check(ctx, load().cdcc_phase_times(ctx.handle,
                                         t.ctypes.data_as(ctypes.c_void_p)))
     return t
+
+
+KERNEL_CLASSES = ("gemm64", "permute", "update", "contract_dL", "other")
+
+
+def cdcc_profile(ctx, enable=True):
+    _check(ctx, load().cdcc_profile(ctx.handle, int(bool(enable))))
+
+
+def cdcc_kernel_stats(ctx, kind):
+    """(device seconds, launches, algorithmic work) of a kernel class."""
+    sec, n, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, load().cdcc_kernel_stats(ctx.handle, int(kind),
+                                         ctypes.byref(sec), ctypes.byref(n),
+                                         ctypes.byref(w)))
+    return sec.value, n.value, w.value
 
 
 def cdcc_kernel_launches(ctx) -> int:

@@ -328,10 +328,13 @@ double probe_step(cdcc_ctx* c, Tensor* R1, Tensor* R2, Tensor* e1) {
   const DevTasks& t1 = e.update_tasks(c->T1->lay);
   const DevTasks& t2 = e.update_tasks(c->T2->lay);
   const int64_t n1 = c->T1->lay.size;
-  e.launches += jacobi_update(t1.tasks, t1.chunks, t1.nchunk, R1->d, nullptr,
-                              e1->d, c->d_eps, c->d_max, c->st);
-  e.launches += jacobi_update(t2.tasks, t2.chunks, t2.nchunk, R2->d, nullptr,
-                              e1->d + n1, c->d_eps, c->d_max, c->st);
+  const double ub = 16.0 * (c->T1->lay.size + c->T2->lay.size);
+  e.timed(Engine::K_UPDATE, ub, [&] {
+    return jacobi_update(t1.tasks, t1.chunks, t1.nchunk, R1->d, nullptr,
+                         e1->d, c->d_eps, c->d_max, c->st) +
+           jacobi_update(t2.tasks, t2.chunks, t2.nchunk, R2->d, nullptr,
+                         e1->d + n1, c->d_eps, c->d_max, c->st);
+  });
   unsigned long long bits = 0;
   CK(cudaMemcpyAsync(&bits, c->d_max, 8, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -367,8 +370,10 @@ void diis_step(cdcc_ctx* c, Diis& D, Tensor* x, Tensor* err) {
   const int m = D.count;
   std::vector<const double*> xs(m);
   for (int k = 0; k < m; ++k) xs[k] = D.e[k]->d;
-  e.launches += multi_dot(xs.data(), m, D.e[s]->d, D.n, c->d_partial,
-                          c->d_dots, c->st);
+  e.timed(Engine::K_OTHER, 8.0 * (m + 1) * D.n, [&] {
+    return multi_dot(xs.data(), m, D.e[s]->d, D.n, c->d_partial, c->d_dots,
+                     c->st);
+  });
   std::vector<double> dots(m);
   CK(cudaMemcpyAsync(dots.data(), c->d_dots, m * 8, cudaMemcpyDeviceToHost,
                      c->st));
@@ -415,7 +420,9 @@ void diis_step(cdcc_ctx* c, Diis& D, Tensor* x, Tensor* err) {
   }
   std::vector<const double*> px(m);
   for (int k = 0; k < m; ++k) px[k] = D.x[k]->d;
-  e.launches += lincomb(x->d, px.data(), sol.data(), m, D.n, c->st);
+  e.timed(Engine::K_OTHER, 8.0 * (m + 1) * D.n, [&] {
+    return lincomb(x->d, px.data(), sol.data(), m, D.n, c->st);
+  });
 }
 
 struct PhaseTimer {
@@ -453,8 +460,9 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
       break;
     e_old = E;
     have_old = true;
-    e.launches += axpby(1.0, c->err1->d, 1.0, c->amp->d, c->amp->lay.size,
-                        c->st);
+    e.timed(Engine::K_OTHER, 24.0 * c->amp->lay.size, [&] {
+      return axpby(1.0, c->err1->d, 1.0, c->amp->d, c->amp->lay.size, c->st);
+    });
     if (it >= 2) diis_step(c, c->cc_diis, c->amp, c->err1);
   }
   pt.stop();
@@ -493,8 +501,9 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
     if (!std::isfinite(rmax))
       throw StatusError(CDCC_ENUMERIC, "non-finite Lambda residual");
     if (rmax <= c->opt.conv_tol) break;
-    e.launches += axpby(1.0, c->err1->d, 1.0, c->lam->d, c->lam->lay.size,
-                        c->st);
+    e.timed(Engine::K_OTHER, 24.0 * c->lam->lay.size, [&] {
+      return axpby(1.0, c->err1->d, 1.0, c->lam->d, c->lam->lay.size, c->st);
+    });
     if (it >= 2) diis_step(c, c->lam_diis, c->lam, c->err1);
   }
   (void)g;
@@ -586,7 +595,10 @@ void run_contract(cdcc_ctx* c, int nx, const int32_t* x_irrep,
                          cudaMemcpyHostToDevice, c->st));
       src = stage;
     }
-    e.launches += batched_dot(c->Gsym->d, src, cnt, nnz, part, d_g, c->st);
+    // algorithmic bytes: each dL_x once plus Gamma once
+    e.timed(Engine::K_DOT, 8.0 * (cnt + 1) * nnz, [&] {
+      return batched_dot(c->Gsym->d, src, cnt, nnz, part, d_g, c->st);
+    });
     CK(cudaMemcpyAsync(gtmp.data(), d_g, cnt * 8, cudaMemcpyDeviceToHost,
                        c->st));
     CK(cudaStreamSynchronize(c->st));
@@ -955,6 +967,26 @@ cdcc_status cdcc_phase_times(cdcc_ctx* c, double* t4) {
   if (!c || !t4) return CDCC_EINVAL;
   for (int i = 0; i < 4; ++i) t4[i] = c->phase[i];
   return CDCC_OK;
+}
+
+cdcc_status cdcc_profile(cdcc_ctx* c, int enable) {
+  if (!c || !c->eng) return CDCC_EINVAL;
+  return guarded(c, [&] {
+    c->eng->prof_collect();
+    c->eng->profile(enable != 0);
+  });
+}
+
+cdcc_status cdcc_kernel_stats(cdcc_ctx* c, int kind, double* seconds,
+                              long long* launches, double* work) {
+  if (!c || !c->eng || kind < 0 || kind >= Engine::K_NKIND)
+    return CDCC_EINVAL;
+  return guarded(c, [&] {
+    c->eng->prof_collect();
+    if (seconds) *seconds = c->eng->prof_sec[kind];
+    if (launches) *launches = (long long)c->eng->prof_n[kind];
+    if (work) *work = c->eng->prof_work[kind];
+  });
 }
 
 long long cdcc_kernel_launches(const cdcc_ctx* c) {

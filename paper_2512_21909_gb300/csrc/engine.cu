@@ -56,6 +56,12 @@ Engine::~Engine() {
     al.release(kv.second.chunks, kv.second.nchunk * sizeof(Chunk));
   }
   for (auto& b : pool_) al.release(b.d, (size_t)b.n * 8);
+  cudaStreamSynchronize(st_);
+  for (auto& r : pending_) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : ev_pool_) cudaEventDestroy(e);
 }
 
 Layout Engine::make_layout(const std::vector<int>& spaces, int split,
@@ -150,6 +156,32 @@ Tensor* Engine::adjoint(Tensor* t) {
     t->adj = tensor(t->name + "~", sp, t->lay.split, t->lay.gtot);
   }
   return t->adj;
+}
+
+cudaEvent_t Engine::get_event() {
+  if (!ev_pool_.empty()) {
+    cudaEvent_t e = ev_pool_.back();
+    ev_pool_.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  ECK(cudaEventCreate(&e));
+  return e;
+}
+
+void Engine::prof_collect() {
+  if (pending_.empty()) return;
+  ECK(cudaStreamSynchronize(st_));
+  for (auto& r : pending_) {
+    float ms = 0;
+    ECK(cudaEventElapsedTime(&ms, r.a, r.b));
+    prof_sec[r.kind] += ms * 1e-3;
+    prof_work[r.kind] += r.work;
+    prof_n[r.kind] += r.n;
+    ev_pool_.push_back(r.a);
+    ev_pool_.push_back(r.b);
+  }
+  pending_.clear();
 }
 
 void Engine::zero(Tensor* t) {
@@ -297,8 +329,14 @@ void Engine::axpy_raw(double alpha, const Layout& XL, const double* X,
   const DevTasks& dt = perm_tasks(YL, XL, xq, false);
   if (dt.embed && beta != 1.0)
     throw EngineError("axpy: embedding requires beta = 1");
-  launches += perm_axpy(dt.tasks, dt.chunks, dt.nchunk, alpha, X, beta, Y,
-                        st_);
+  int64_t nel = 0;
+  if (prof_on_) {
+    // bytes: read X, write Y (+ read Y when accumulating)
+    nel = (beta == 0.0 ? 16 : 24) * (dt.embed ? XL.size : YL.size);
+  }
+  timed(K_PERM, (double)nel, [&] {
+    return perm_axpy(dt.tasks, dt.chunks, dt.nchunk, alpha, X, beta, Y, st_);
+  });
 }
 
 void Engine::axpy(double alpha, Tensor* X, const char* ix, double beta,
@@ -499,7 +537,12 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   }
   const int64_t sk = gemm_scratch_doubles(probs, np);
   double* skb = sk > 0 ? scratch(sk) : nullptr;
-  launches += gemm64_grouped(probs, np, alpha, direct ? beta : 0.0, skb, st_);
+  double fl = 0;
+  for (int i = 0; i < np; ++i)
+    fl += 2.0 * probs[i].M * (double)probs[i].N * probs[i].K;
+  timed(K_GEMM64, fl, [&] {
+    return gemm64_grouped(probs, np, alpha, direct ? beta : 0.0, skb, st_);
+  });
   if (!direct)
     axpy_raw(1.0, *DL, Dd, best.X + best.Y, beta, C->lay, C->d, ic);
   release_scratch();

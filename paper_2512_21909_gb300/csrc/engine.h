@@ -108,6 +108,28 @@ class Engine {
   int64_t launches = 0;
   int64_t flops = 0;  // FP64 GEMM flops issued
 
+  // Optional per-kernel-class timing with CUDA events on the engine stream.
+  enum ProfKind : int { K_GEMM64 = 0, K_PERM = 1, K_UPDATE = 2, K_DOT = 3,
+                        K_OTHER = 4, K_NKIND = 5 };
+  void profile(bool on) { prof_on_ = on; }
+  template <class F>
+  void timed(int kind, double work, F launch) {
+    if (!prof_on_) {
+      launches += launch();
+      return;
+    }
+    cudaEvent_t a = get_event(), b = get_event();
+    cudaEventRecord(a, st_);
+    const int n = launch();
+    cudaEventRecord(b, st_);
+    launches += n;
+    pending_.push_back({kind, a, b, work, n});
+    if (pending_.size() > 8192) prof_collect();
+  }
+  void prof_collect();
+  double prof_sec[K_NKIND] = {}, prof_work[K_NKIND] = {};
+  int64_t prof_n[K_NKIND] = {};
+
   DevAlloc al;
 
  private:
@@ -146,6 +168,16 @@ class Engine {
   };
   std::vector<Buf> pool_;
   std::vector<std::unique_ptr<Layout>> tmp_layouts_;
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double work;
+    int n;
+  };
+  cudaEvent_t get_event();
+  bool prof_on_ = false;
+  std::vector<ProfRec> pending_;
+  std::vector<cudaEvent_t> ev_pool_;
 };
 
 }  // namespace cdcc
