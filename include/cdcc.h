@@ -155,6 +155,36 @@ cdcc_status contract_dL(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
 cdcc_status gradient(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
                      const double *dL, double *e_corr, double *g);
 
+/*
+ * contract_dL without any memory allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * code embedded in a host framework or plugin whose device memory is owned
+ * and budgeted by someone else, and serving loops that must not call
+ * cudaMalloc because it synchronises the whole device.
+ *
+ * Computes g[x] = sum_e gamma[e] * dL[x*nnz + e] for x < nx, i.e. the same
+ * contraction as contract_dL for totally symmetric displacements, where
+ * gamma is the packed Gamma^P_pq (see cdcc_get_gamma) and dL holds nx packed
+ * derivative tensors back to back.
+ *   gamma, dL, g  DEVICE pointers of the current device, owned by the caller
+ *   nx            1 .. CDCC_NOALLOC_MAX_NX, else CDCC_EINVAL
+ *   nnz           elements per packed tensor (>= 1)
+ *   stream        cudaStream_t (may be 0); the call only enqueues work, g is
+ *                 valid once the stream reaches that point
+ * No cudaMalloc / cudaFree or allocating library routine is called.  The
+ * per-block partial sums live in a fixed device array of
+ * 1216 x CDCC_NOALLOC_MAX_NX doubles (608 KiB) that every device loading the
+ * library keeps until exit.  The first call on a device looks that array's
+ * address up (with the device current), so make it before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * race on it and must be serialised.  Non-device pointers return
+ * CDCC_EINVAL; a failed launch returns CDCC_ECUDA.
+ */
+#define CDCC_NOALLOC_MAX_NX 64
+cdcc_status cdcc_contract_dL_noalloc(const double *gamma, const double *dL,
+                                     int nx, size_t nnz, double *g,
+                                     void *stream);
+
 /* Amplitude / multiplier export for checks and warm starts:
  * which = 0: t1 [nocc][nvir], 1: t2 [nocc][nocc][nvir][nvir],
  *         2: lambda1, 3: lambda2 (same shapes; dense, zeros off-symmetry).

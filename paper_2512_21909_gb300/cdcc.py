@@ -318,6 +318,28 @@ def cd_ccsd_free(ctx):
     ctx.close()
 
 
+def cdcc_contract_dL_noalloc(gamma, dL, nx, nnz, g, stream=None):
+    """Allocation-free contract_dL on caller-owned CUDA tensors (gamma: packed
+    Gamma, dL: nx packed tensors, g: nx outputs); enqueues on `stream`
+    (default: the current torch stream) and returns without waiting."""
+    lib = load()
+    if not hasattr(lib, "_noalloc_typed"):
+        lib.cdcc_contract_dL_noalloc.argtypes = [
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t,
+            ctypes.c_void_p, ctypes.c_void_p]
+        lib.cdcc_contract_dL_noalloc.restype = ctypes.c_int
+        lib._noalloc_typed = True
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.cdcc_contract_dL_noalloc(
+        ctypes.c_void_p(gamma.data_ptr()), ctypes.c_void_p(dL.data_ptr()),
+        int(nx), int(nnz), ctypes.c_void_p(g.data_ptr()),
+        ctypes.c_void_p(int(stream)))
+    if st != CDCC_OK:
+        raise CdccError(st, "cdcc_contract_dL_noalloc failed")
+
+
 def init_from_system(sysm, **kw) -> Context:
     """cd_ccsd_init from a synth.System (host arrays)."""
     return cd_ccsd_init(sysm.nirrep, sysm.nocc, sysm.nvir, sysm.nchol,
