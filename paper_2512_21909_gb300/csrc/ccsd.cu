@@ -131,6 +131,7 @@ struct cdcc_ctx {
   Tensor *hoo, *hov, *hvo, *hvv, *Ioo;
   Tensor *amp, *T1, *T2, *res, *R1, *R2, *err1, *lam, *L1, *L2, *E;
   Tensor *Gam = nullptr, *Gsym = nullptr, *D1a = nullptr, *D1s = nullptr;
+  Tensor *Govov = nullptr, *Govvv = nullptr, *W0 = nullptr;
   Diis cc_diis, lam_diis;
 };
 
@@ -175,6 +176,20 @@ void upload_dense(cdcc_ctx* c, Tensor* t, const std::vector<double>& dense) {
   CK(cudaMemcpyAsync(t->d, p.data(), p.size() * 8, cudaMemcpyHostToDevice,
                      c->st));
   CK(cudaStreamSynchronize(c->st));
+}
+
+// ------------------------------------------------------------------ prepare
+// Amplitude-independent integrals, built once per gradient (and recorded at
+// the head of the tape so that the density sweep differentiates them):
+//   (ia|jb), (mc|bd) and the undressed ladder integrals W0[a,b,c,d]=(ac|bd).
+void prepare(cdcc_ctx* c) {
+  Engine& e = *c->eng;
+  c->Govov = e.tensor("Govov", {SO, SV, SO, SV}, 2);
+  e.contract(1.0, c->Lov, "Pia", c->Lov, "Pjb", 0.0, c->Govov, "iajb");
+  c->Govvv = e.tensor("Govvv", {SO, SV, SV, SV}, 2);
+  e.contract(1.0, c->Lov, "Pmc", c->Lvv, "Pbd", 0.0, c->Govvv, "mcbd");
+  c->W0 = e.tensor("W0", {SV, SV, SV, SV}, 2);
+  e.contract(1.0, c->Lvv, "Pac", c->Lvv, "Pbd", 0.0, c->W0, "abcd");
 }
 
 // ------------------------------------------------------------------ residual
@@ -235,9 +250,9 @@ void residual(cdcc_ctx* c) {
   e.contract(2.0, Lhvv, "Pab", J, "P", 1.0, Fvv, "ab");
   e.contract(-1.0, Lhvo, "Pak", Lov, "Pkb", 1.0, Fvv, "ab");
 
-  // Cholesky-built integrals (Eq. 1), Mulliken order
-  Tensor* Govov = T("Govov", {SO, SV, SO, SV}, 2);
-  e.contract(1.0, Lov, "Pia", Lov, "Pjb", 0.0, Govov, "iajb");
+  // Cholesky-built integrals (Eq. 1), Mulliken order; (ia|jb), (mc|bd) and
+  // the undressed ladder integrals are amplitude independent (prepare()).
+  Tensor* Govov = c->Govov;
   Tensor* Gvovo = T("Gvovo", {SV, SO, SV, SO}, 2);
   e.contract(1.0, Lhvo, "Pai", Lhvo, "Pbj", 0.0, Gvovo, "aibj");
   Tensor* Goooo = T("Goooo", {SO, SO, SO, SO}, 2);
@@ -246,9 +261,6 @@ void residual(cdcc_ctx* c) {
   e.contract(1.0, Lhoo, "Pki", Lhvv, "Pac", 0.0, Goovv, "kiac");
   Tensor* Govvo = T("Govvo", {SO, SV, SV, SO}, 2);
   e.contract(1.0, Lov, "Pme", Lhvo, "Pbj", 0.0, Govvo, "mebj");
-  // particle-particle ladder integrals (ac|bd), built from Lhat_vv
-  Tensor* Wvvvv = T("Wvvvv", {SV, SV, SV, SV}, 2);
-  e.contract(1.0, Lhvv, "Pac", Lhvv, "Pbd", 0.0, Wvvvv, "acbd");
 
   Tensor* u = T("u", {SO, SO, SV, SV}, 2);
   e.axpy(2.0, t2s, "ijab", 0.0, u, "ijab");
@@ -268,7 +280,20 @@ void residual(cdcc_ctx* c) {
   // ---- doubles
   Tensor* Rr = T("R2raw", {SO, SO, SV, SV}, 2);
   e.axpy(1.0, Gvovo, "aibj", 0.0, Rr, "ijab");
-  e.contract(1.0, t2s, "ijcd", Wvvvv, "acbd", 1.0, Rr, "ijab");  // PPL
+  // particle-particle ladder with the dressed (ac|bd)^ = sum_P Lhat_ac Lhat_bd,
+  // Lhat_vv = L_vv - t1^T L_ov, expanded so that only the undressed W0 (built
+  // once per gradient) enters the O(o^2 v^4) product:
+  //   (ac|bd)^ = (ac|bd) - t_m^a (mc|bd) - t_n^b (ac|nd) + t_m^a t_n^b (mc|nd)
+  e.contract(1.0, t2s, "ijcd", c->W0, "abcd", 1.0, Rr, "ijab");  // PPL
+  Tensor* Yl = T("Ylad", {SO, SO, SO, SV}, 2);
+  e.contract(1.0, t2s, "ijcd", c->Govvv, "mcbd", 0.0, Yl, "ijmb");
+  e.contract(-1.0, T1, "ma", Yl, "ijmb", 1.0, Rr, "ijab");
+  e.contract(-1.0, T1, "nb", Yl, "jina", 1.0, Rr, "ijab");
+  Tensor* Zl = T("Zlad", {SO, SO, SO, SO}, 2);
+  e.contract(1.0, t2s, "ijcd", Govov, "mcnd", 0.0, Zl, "ijmn");
+  Tensor* Xl = T("Xlad", {SO, SO, SV, SO}, 2);
+  e.contract(1.0, T1, "ma", Zl, "ijmn", 0.0, Xl, "ijan");
+  e.contract(1.0, T1, "nb", Xl, "ijan", 1.0, Rr, "ijab");
   Tensor* Wh = T("Whh", {SO, SO, SO, SO}, 2);
   e.axpy(1.0, Goooo, "kilj", 0.0, Wh, "kilj");
   e.contract(1.0, t2s, "ijcd", Govov, "kcld", 1.0, Wh, "kilj");
@@ -444,6 +469,7 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 0);
   e.zero(c->amp);
+  prepare(c);
   c->tape_ready = false;
   diis_init(c, c->cc_diis, "ccdiis", c->amp->lay.size);
   double e_old = 0, rmax = 0, E = 0;
@@ -479,6 +505,7 @@ void ensure_tape(cdcc_ctx* c) {
   if (c->tape_ready) return;
   c->eng->clear_tape();
   c->eng->record(true);
+  prepare(c);
   residual(c);
   c->eng->record(false);
   c->tape_ready = true;

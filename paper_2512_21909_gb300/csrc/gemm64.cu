@@ -1,0 +1,303 @@
+// gemm64.cu -- grouped FP64 GEMM (DFMA, SIMT) for the FP64 path.
+//
+// GB300 executes 2 DFMA per clock per SM, so an FP64 GEMM is bound by the
+// FP64 pipe, not by memory: the kernel only has to keep that pipe busy.
+// Tiles are BM x BN x 16 (BM, BN in {32, 64}; 256 threads, (BM/16) x (BN/16)
+// outputs per thread), staged through shared memory with register double
+// buffering.  The tile shape is chosen per grouped launch from the largest
+// block (thin pair blocks such as N_oo = 32 rows would waste half of a 64-row
+// tile), and thin products are split along K so that about four CTAs per SM
+// are available; split-K partials are summed in a fixed order (deterministic).
+#include <algorithm>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace cdcc {
+
+namespace {
+
+constexpr int BK = 16, NT = 256;
+constexpr int SMS = 152;
+
+struct GemmLaunch {
+  GemmProb p[GEMM_MAXPROB];
+  int tile0[GEMM_MAXPROB + 1];
+  int tm[GEMM_MAXPROB], tn[GEMM_MAXPROB], ks[GEMM_MAXPROB];
+  int64_t poff[GEMM_MAXPROB];
+  int np;
+  double alpha, beta;
+  double* scratch;
+};
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(NT)
+    gemm64_kernel(const __grid_constant__ GemmLaunch L) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int bid = blockIdx.x;
+  int pi = 0;
+  while (pi + 1 < L.np && bid >= L.tile0[pi + 1]) ++pi;
+  const GemmProb& P = L.p[pi];
+  int local = bid - L.tile0[pi];
+  const int ksn = L.ks[pi];
+  const int ks = local % ksn;
+  local /= ksn;
+  const int tn = local % L.tn[pi];
+  const int tm = local / L.tn[pi];
+  const int m0 = tm * BM, n0 = tn * BN;
+  int kper = (P.K + ksn - 1) / ksn;
+  kper = (kper + BK - 1) / BK * BK;
+  const int kbeg = ks * kper;
+  const int kend = min(P.K, kbeg + kper);
+  const int t = threadIdx.x;
+  const int tx = t & 15, ty = t >> 4;
+
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  double ra[TM], rb[TN];
+  auto load = [&](int k0) {
+    if (!P.ta) {  // A[m][k], k contiguous
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int m = m0 + (t >> 4) + 16 * i, k = k0 + (t & 15);
+        ra[i] = (m < P.M && k < kend) ? P.A[(int64_t)m * P.lda + k] : 0.0;
+      }
+    } else {      // A stored [k][m], m contiguous
+      constexpr int KS = NT / BM;
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        const int m = m0 + t % BM, k = k0 + t / BM + KS * i;
+        ra[i] = (m < P.M && k < kend) ? P.A[(int64_t)k * P.lda + m] : 0.0;
+      }
+    }
+    if (!P.tb) {  // B[k][n], n contiguous
+      constexpr int KS = NT / BN;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + t % BN, k = k0 + t / BN + KS * j;
+        rb[j] = (n < P.N && k < kend) ? P.B[(int64_t)k * P.ldb + n] : 0.0;
+      }
+    } else {      // B stored [n][k], k contiguous
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + (t >> 4) + 16 * j, k = k0 + (t & 15);
+        rb[j] = (n < P.N && k < kend) ? P.B[(int64_t)n * P.ldb + k] : 0.0;
+      }
+    }
+  };
+  auto store = [&]() {
+    if (!P.ta) {
+#pragma unroll
+      for (int i = 0; i < TM; ++i) As[t & 15][(t >> 4) + 16 * i] = ra[i];
+    } else {
+      constexpr int KS = NT / BM;
+#pragma unroll
+      for (int i = 0; i < TM; ++i) As[t / BM + KS * i][t % BM] = ra[i];
+    }
+    if (!P.tb) {
+      constexpr int KS = NT / BN;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) Bs[t / BN + KS * j][t % BN] = rb[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < TN; ++j) Bs[t & 15][(t >> 4) + 16 * j] = rb[j];
+    }
+  };
+
+  if (kbeg < kend) load(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    __syncthreads();
+    store();
+    __syncthreads();
+    if (k0 + BK < kend) load(k0 + BK);
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  if (ksn == 1) {
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + ty + 16 * i;
+      if (m >= P.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n >= P.N) continue;
+        double* c = P.C + (int64_t)m * P.ldc + n;
+        const double v = L.alpha * acc[i][j];
+        *c = (L.beta == 0.0) ? v : fma(L.beta, *c, v);
+      }
+    }
+  } else {
+    double* part = L.scratch + L.poff[pi] + (int64_t)ks * P.M * P.N;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + ty + 16 * i;
+      if (m >= P.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tx + 16 * j;
+        if (n >= P.N) continue;
+        part[(int64_t)m * P.N + n] = acc[i][j];
+      }
+    }
+  }
+}
+
+struct ReduceLaunch {
+  double* C[GEMM_MAXPROB];
+  int M[GEMM_MAXPROB], N[GEMM_MAXPROB], ldc[GEMM_MAXPROB], ks[GEMM_MAXPROB];
+  int64_t poff[GEMM_MAXPROB];
+  int64_t elem0[GEMM_MAXPROB + 1];
+  int np;
+  double alpha, beta;
+  const double* scratch;
+};
+
+__global__ void splitk_reduce_kernel(const __grid_constant__ ReduceLaunch R) {
+  const int64_t total = R.elem0[R.np];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int pi = 0;
+    while (pi + 1 < R.np && e >= R.elem0[pi + 1]) ++pi;
+    const int64_t loc = e - R.elem0[pi];
+    const int m = (int)(loc / R.N[pi]), n = (int)(loc % R.N[pi]);
+    const int64_t MN = (int64_t)R.M[pi] * R.N[pi];
+    const double* part = R.scratch + R.poff[pi] + loc;
+    double s = 0.0;
+    for (int k = 0; k < R.ks[pi]; ++k) s += part[k * MN];
+    double* c = R.C[pi] + (int64_t)m * R.ldc[pi] + n;
+    const double v = R.alpha * s;
+    *c = (R.beta == 0.0) ? v : fma(R.beta, *c, v);
+  }
+}
+
+struct Plan {
+  int bm, bn;
+  int tm[GEMM_MAXPROB], tn[GEMM_MAXPROB], ks[GEMM_MAXPROB];
+  int64_t scratch;
+};
+
+// Tile shape from the largest block; split K until ~4 CTAs per SM exist.
+Plan make_plan(const GemmProb* p, int np) {
+  Plan pl;
+  std::memset(&pl, 0, sizeof(pl));
+  int maxM = 0, maxN = 0;
+  for (int i = 0; i < np; ++i)
+    if (p[i].M > 0 && p[i].N > 0) {
+      maxM = std::max(maxM, p[i].M);
+      maxN = std::max(maxN, p[i].N);
+    }
+  pl.bm = maxM <= 40 ? 32 : 64;
+  pl.bn = maxN <= 40 ? 32 : 64;
+  int64_t tiles = 0;
+  for (int i = 0; i < np; ++i) {
+    if (p[i].M <= 0 || p[i].N <= 0) continue;
+    pl.tm[i] = (p[i].M + pl.bm - 1) / pl.bm;
+    pl.tn[i] = (p[i].N + pl.bn - 1) / pl.bn;
+    tiles += (int64_t)pl.tm[i] * pl.tn[i];
+  }
+  const int64_t want = 4 * SMS;
+  for (int i = 0; i < np; ++i) {
+    pl.ks[i] = 1;
+    if (p[i].M <= 0 || p[i].N <= 0) continue;
+    if (tiles < want && p[i].K >= 256) {
+      int ks = (int)((want + tiles - 1) / std::max<int64_t>(tiles, 1));
+      ks = std::min(ks, std::max(1, p[i].K / 128));
+      ks = std::min(ks, 64);
+      pl.ks[i] = std::max(1, ks);
+    }
+    if (pl.ks[i] > 1)
+      pl.scratch += (int64_t)pl.ks[i] * p[i].M * p[i].N;
+  }
+  return pl;
+}
+
+template <int BM, int BN>
+void launch_tile(const GemmLaunch& L, int tiles, cudaStream_t st) {
+  gemm64_kernel<BM, BN><<<tiles, NT, 0, st>>>(L);
+}
+
+}  // namespace
+
+int64_t gemm_scratch_doubles(const GemmProb* p, int np) {
+  return make_plan(p, np).scratch;
+}
+
+int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
+                   double* scratch, cudaStream_t st) {
+  const Plan pl = make_plan(p, np);
+  GemmLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  ReduceLaunch R;
+  std::memset(&R, 0, sizeof(R));
+  L.alpha = alpha;
+  L.beta = beta;
+  L.scratch = scratch;
+  R.alpha = alpha;
+  R.beta = beta;
+  R.scratch = scratch;
+  int n = 0, nr = 0, tiles = 0;
+  int64_t poff = 0, relem = 0;
+  for (int i = 0; i < np; ++i) {
+    if (p[i].M <= 0 || p[i].N <= 0) continue;
+    const int ks = pl.ks[i];
+    L.p[n] = p[i];
+    L.tm[n] = pl.tm[i];
+    L.tn[n] = pl.tn[i];
+    L.ks[n] = ks;
+    L.tile0[n] = tiles;
+    L.poff[n] = ks > 1 ? poff : 0;
+    tiles += pl.tm[i] * pl.tn[i] * ks;
+    if (ks > 1) {
+      R.C[nr] = p[i].C;
+      R.M[nr] = p[i].M;
+      R.N[nr] = p[i].N;
+      R.ldc[nr] = p[i].ldc;
+      R.ks[nr] = ks;
+      R.poff[nr] = poff;
+      R.elem0[nr] = relem;
+      relem += (int64_t)p[i].M * p[i].N;
+      poff += (int64_t)ks * p[i].M * p[i].N;
+      ++nr;
+    }
+    ++n;
+  }
+  if (n == 0) return 0;
+  L.np = n;
+  L.tile0[n] = tiles;
+  if (pl.bm == 32 && pl.bn == 32)
+    launch_tile<32, 32>(L, tiles, st);
+  else if (pl.bm == 32)
+    launch_tile<32, 64>(L, tiles, st);
+  else if (pl.bn == 32)
+    launch_tile<64, 32>(L, tiles, st);
+  else
+    launch_tile<64, 64>(L, tiles, st);
+  int launches = 1;
+  if (nr > 0) {
+    R.np = nr;
+    R.elem0[nr] = relem;
+    const int blocks = (int)std::min<int64_t>((relem + 255) / 256, 4096);
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(R);
+    ++launches;
+  }
+  return launches;
+}
+
+}  // namespace cdcc

@@ -1,10 +1,5 @@
-// kernels.cu -- FP64 grouped GEMM, DPD permute / update, reductions.
-//
-// The FP64 GEMM is a plain DFMA SIMT kernel (64x64x16 tiles, 256 threads,
-// 4x4 outputs per thread, shared-memory staging, register double buffering).
-// All irrep blocks of one contraction go through one grouped launch; thin
-// products (few output tiles, long K) are split along K with a deterministic
-// second-pass reduction.
+// kernels.cu -- DPD permute / update, reductions, batched dot (the FP64 GEMM
+// is in gemm64.cu).
 #include "kernels.h"
 
 #include <algorithm>
@@ -14,284 +9,11 @@ namespace cdcc {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 constexpr int CHUNK = 4096;
-
-struct GemmLaunch {
-  GemmProb p[GEMM_MAXPROB];
-  int tile0[GEMM_MAXPROB + 1];
-  int tm[GEMM_MAXPROB], tn[GEMM_MAXPROB], ks[GEMM_MAXPROB];
-  int64_t poff[GEMM_MAXPROB];
-  int np;
-  double alpha, beta;
-  double* scratch;
-};
-
-__device__ __forceinline__ void load_tile_a(const GemmProb& P, int m0, int k0,
-                                            int kend, double (&ra)[4]) {
-  const int t = threadIdx.x;
-  if (!P.ta) {
-    const int c = t & 15;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = (t >> 4) + 16 * i;
-      const int m = m0 + r, k = k0 + c;
-      ra[i] = (m < P.M && k < kend) ? P.A[(int64_t)m * P.lda + k] : 0.0;
-    }
-  } else {
-    const int c = t & 63;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = (t >> 6) + 4 * i;
-      const int m = m0 + c, k = k0 + r;
-      ra[i] = (m < P.M && k < kend) ? P.A[(int64_t)k * P.lda + m] : 0.0;
-    }
-  }
-}
-
-__device__ __forceinline__ void store_tile_a(const GemmProb& P,
-                                             double (*As)[BM + 1],
-                                             const double (&ra)[4]) {
-  const int t = threadIdx.x;
-  if (!P.ta) {
-    const int c = t & 15;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) As[c][(t >> 4) + 16 * i] = ra[i];
-  } else {
-    const int c = t & 63;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) As[(t >> 6) + 4 * i][c] = ra[i];
-  }
-}
-
-__device__ __forceinline__ void load_tile_b(const GemmProb& P, int n0, int k0,
-                                            int kend, double (&rb)[4]) {
-  const int t = threadIdx.x;
-  if (!P.tb) {
-    const int c = t & 63;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = (t >> 6) + 4 * i;
-      const int n = n0 + c, k = k0 + r;
-      rb[i] = (n < P.N && k < kend) ? P.B[(int64_t)k * P.ldb + n] : 0.0;
-    }
-  } else {
-    const int c = t & 15;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = (t >> 4) + 16 * i;
-      const int n = n0 + r, k = k0 + c;
-      rb[i] = (n < P.N && k < kend) ? P.B[(int64_t)n * P.ldb + k] : 0.0;
-    }
-  }
-}
-
-__device__ __forceinline__ void store_tile_b(const GemmProb& P,
-                                             double (*Bs)[BN + 1],
-                                             const double (&rb)[4]) {
-  const int t = threadIdx.x;
-  if (!P.tb) {
-    const int c = t & 63;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) Bs[(t >> 6) + 4 * i][c] = rb[i];
-  } else {
-    const int c = t & 15;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) Bs[c][(t >> 4) + 16 * i] = rb[i];
-  }
-}
-
-__global__ void __launch_bounds__(NT)
-    gemm64_kernel(const __grid_constant__ GemmLaunch L) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
-  const int bid = blockIdx.x;
-  int pi = 0;
-  while (pi + 1 < L.np && bid >= L.tile0[pi + 1]) ++pi;
-  const GemmProb& P = L.p[pi];
-  int local = bid - L.tile0[pi];
-  const int ksn = L.ks[pi];
-  const int ks = local % ksn;
-  local /= ksn;
-  const int tn = local % L.tn[pi];
-  const int tm = local / L.tn[pi];
-  const int m0 = tm * BM, n0 = tn * BN;
-  int kper = (P.K + ksn - 1) / ksn;
-  kper = (kper + BK - 1) / BK * BK;
-  const int kbeg = ks * kper;
-  const int kend = min(P.K, kbeg + kper);
-
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-
-  double ra[4], rb[4];
-  if (kbeg < kend) {
-    load_tile_a(P, m0, kbeg, kend, ra);
-    load_tile_b(P, n0, kbeg, kend, rb);
-  }
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    __syncthreads();
-    store_tile_a(P, As, ra);
-    store_tile_b(P, Bs, rb);
-    __syncthreads();
-    if (k0 + BK < kend) {
-      load_tile_a(P, m0, k0 + BK, kend, ra);
-      load_tile_b(P, n0, k0 + BK, kend, rb);
-    }
-#pragma unroll
-    for (int k = 0; k < BK; ++k) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-  }
-  if (ksn == 1) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int m = m0 + ty + 16 * i;
-      if (m >= P.M) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = n0 + tx + 16 * j;
-        if (n >= P.N) continue;
-        double* c = P.C + (int64_t)m * P.ldc + n;
-        const double v = L.alpha * acc[i][j];
-        *c = (L.beta == 0.0) ? v : fma(L.beta, *c, v);
-      }
-    }
-  } else {
-    double* part = L.scratch + L.poff[pi] + (int64_t)ks * P.M * P.N;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int m = m0 + ty + 16 * i;
-      if (m >= P.M) continue;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = n0 + tx + 16 * j;
-        if (n >= P.N) continue;
-        part[(int64_t)m * P.N + n] = acc[i][j];
-      }
-    }
-  }
-}
-
-struct ReduceLaunch {
-  double* C[GEMM_MAXPROB];
-  int M[GEMM_MAXPROB], N[GEMM_MAXPROB], ldc[GEMM_MAXPROB], ks[GEMM_MAXPROB];
-  int64_t poff[GEMM_MAXPROB];
-  int64_t elem0[GEMM_MAXPROB + 1];
-  int np;
-  double alpha, beta;
-  const double* scratch;
-};
-
-__global__ void splitk_reduce_kernel(const __grid_constant__ ReduceLaunch R) {
-  const int64_t total = R.elem0[R.np];
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int pi = 0;
-    while (pi + 1 < R.np && e >= R.elem0[pi + 1]) ++pi;
-    const int64_t loc = e - R.elem0[pi];
-    const int m = (int)(loc / R.N[pi]), n = (int)(loc % R.N[pi]);
-    const int64_t MN = (int64_t)R.M[pi] * R.N[pi];
-    const double* part = R.scratch + R.poff[pi] + loc;
-    double s = 0.0;
-    for (int k = 0; k < R.ks[pi]; ++k) s += part[k * MN];
-    double* c = R.C[pi] + (int64_t)m * R.ldc[pi] + n;
-    const double v = R.alpha * s;
-    *c = (R.beta == 0.0) ? v : fma(R.beta, *c, v);
-  }
-}
-
-void plan_splitk(const GemmProb& p, int& tm, int& tn, int& ks) {
-  tm = (p.M + BM - 1) / BM;
-  tn = (p.N + BN - 1) / BN;
-  ks = 1;
-  const int tiles = tm * tn;
-  if (tiles < 64 && p.K >= 2048) {
-    ks = std::min((int)((p.K + 1023) / 1024), std::max(1, 256 / tiles));
-    ks = std::max(1, std::min(ks, 512));
-  }
-}
 
 }  // namespace
 
 int chunk_elems() { return CHUNK; }
-
-int64_t gemm_scratch_doubles(const GemmProb* p, int np) {
-  int64_t s = 0;
-  for (int i = 0; i < np; ++i) {
-    if (p[i].M <= 0 || p[i].N <= 0) continue;
-    int tm, tn, ks;
-    plan_splitk(p[i], tm, tn, ks);
-    if (ks > 1) s += (int64_t)ks * p[i].M * p[i].N;
-  }
-  return s;
-}
-
-int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
-                   double* scratch, cudaStream_t st) {
-  GemmLaunch L;
-  std::memset(&L, 0, sizeof(L));
-  ReduceLaunch R;
-  std::memset(&R, 0, sizeof(R));
-  L.alpha = alpha;
-  L.beta = beta;
-  L.scratch = scratch;
-  R.alpha = alpha;
-  R.beta = beta;
-  R.scratch = scratch;
-  int n = 0, nr = 0, tiles = 0;
-  int64_t poff = 0, relem = 0;
-  for (int i = 0; i < np; ++i) {
-    if (p[i].M <= 0 || p[i].N <= 0) continue;
-    int tm, tn, ks;
-    plan_splitk(p[i], tm, tn, ks);
-    L.p[n] = p[i];
-    L.tm[n] = tm;
-    L.tn[n] = tn;
-    L.ks[n] = ks;
-    L.tile0[n] = tiles;
-    L.poff[n] = ks > 1 ? poff : 0;
-    tiles += tm * tn * ks;
-    if (ks > 1) {
-      R.C[nr] = p[i].C;
-      R.M[nr] = p[i].M;
-      R.N[nr] = p[i].N;
-      R.ldc[nr] = p[i].ldc;
-      R.ks[nr] = ks;
-      R.poff[nr] = poff;
-      R.elem0[nr] = relem;
-      relem += (int64_t)p[i].M * p[i].N;
-      poff += (int64_t)ks * p[i].M * p[i].N;
-      ++nr;
-    }
-    ++n;
-  }
-  if (n == 0) return 0;
-  L.np = n;
-  L.tile0[n] = tiles;
-  gemm64_kernel<<<tiles, NT, 0, st>>>(L);
-  int launches = 1;
-  if (nr > 0) {
-    R.np = nr;
-    R.elem0[nr] = relem;
-    const int blocks = (int)std::min<int64_t>((relem + 255) / 256, 4096);
-    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(R);
-    ++launches;
-  }
-  return launches;
-}
 
 // ----------------------------------------------------------- permute / axpy
 namespace {
