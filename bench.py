@@ -233,7 +233,7 @@ def run_ours(args, rank, ws):
         e, g = cdcc.gradient(ctx, dLsrc)
         stats = None
         if profile:
-            stats = [cdcc.cdcc_kernel_stats(ctx, k) for k in range(5)]
+            stats = [cdcc.cdcc_kernel_stats(ctx, k) for k in range(6)]
         nl = cdcc.cdcc_kernel_launches(ctx)
         ph = cdcc.cdcc_phase_times(ctx)
         cdcc.cd_ccsd_free(ctx)
@@ -249,7 +249,7 @@ def run_ours(args, rank, ws):
     barrier(ws)
     torch.cuda.synchronize()
     times, launches = [], 0
-    agg = np.zeros((5, 3))
+    agg = np.zeros((6, 3))
     for _ in range(args.steps):
         flush.fill_(1.0)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -266,6 +266,31 @@ def run_ours(args, rank, ws):
     clocks = clk.stop()
     t50 = allmax(float(np.median(times)), ws)
     t99 = allmax(float(np.percentile(times, 99)), ws)
+
+    # ---- the other precision on the same workload (mixed vs FP64 GPU)
+    other = "mixed" if args.precision == "fp64" else "fp64"
+    saved = args.precision
+    args.precision = other
+    one(L_d, dL_d)                       # warm-up of the other schedule
+    o_times, o_e, o_g, o_info = [], None, None, None
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        o_e, o_g, _, o_stats, _ = one(L_d, dL_d, profile=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        o_times.append(ev0.elapsed_time(ev1) * 1e-3)
+    args.precision = saved
+    other_line = {"precision": other,
+                  "time_to_gradient_s": float(np.median(o_times)),
+                  "abs_dE_vs_this_run": abs(o_e - e),
+                  "max_abs_dg_vs_this_run": float(np.abs(o_g - g).max()),
+                  "tc_gemm_s": o_stats[5][0] if o_stats else None,
+                  "tc_gemm_tflops": (o_stats[5][2] / o_stats[5][0] / 1e12
+                                     if o_stats and o_stats[5][0] > 0
+                                     else None)}
 
     # ---- end to end through the C ABI with host buffers
     e2e = []
@@ -295,7 +320,7 @@ def run_ours(args, rank, ws):
             cpu = {"error": str(ex)}
     classes = {}
     for k, nm in enumerate(["gemm64", "permute", "update", "contract_dL",
-                            "other"]):
+                            "other", "tc_gemm"]):
         sec, n, w = agg[k]
         classes[nm] = {"seconds": sec / args.steps, "launches": int(n /
                                                                     args.steps),
@@ -321,6 +346,7 @@ def run_ours(args, rank, ws):
                      "peak_source": "nominal GB300 FP64 from the profiling "
                                     "recipe (not in MEASURED_PEAKS.json)",
                      "traffic": None},
+        "other_precision": other_line,
         "e2e": {"value": e2e50, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,

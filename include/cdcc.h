@@ -201,12 +201,32 @@ cdcc_status cdcc_phase_times(cdcc_ctx *ctx, double *t4);
  * every launch of the class while enabled).  Classes:
  *   0 FP64 GEMM (work = flops)          1 permutation / axpy (work = bytes)
  *   2 amplitude update (work = bytes)   3 contract_dL batched dot (bytes)
- *   4 other vector kernels (bytes)
+ *   4 other vector kernels (bytes)     5 tensor-core GEMM (work = flops)
  * cdcc_kernel_stats returns the accumulated device seconds, launches and
  * algorithmic work since the context was created. */
 cdcc_status cdcc_profile(cdcc_ctx *ctx, int enable);
 cdcc_status cdcc_kernel_stats(cdcc_ctx *ctx, int kind, double *seconds,
                               long long *launches, double *work);
+
+/* Iterations of the last solves: info[0..3] = CCSD mixed-precision,
+ * CCSD FP64, Lambda mixed-precision, Lambda FP64 iterations. */
+cdcc_status cdcc_solver_info(cdcc_ctx *ctx, int *info);
+
+/*
+ * C = beta*C + alpha * op(A) op(B) on device buffers, row-major, with the
+ * library's contraction kernels (the building block of every contraction of
+ * the path; exposed for testing and reuse).  op(A) is M x K (transA: A is
+ * stored K x M), op(B) is K x N (transB: B is stored N x K).
+ *   mode 0      FP64 DFMA GEMM
+ *   mode 1..3   tensor-core GEMM with 1..3 BF16 slices per operand
+ *               (products of slices i + j < mode, FP32 accumulation)
+ * Allocates its temporaries with cudaMallocAsync on `stream` and
+ * synchronises the stream before returning.
+ */
+cdcc_status cdcc_dgemm(int transA, int transB, int M, int N, int K,
+                       double alpha, const double *A, int lda,
+                       const double *B, int ldb, double beta, double *C,
+                       int ldc, int mode, void *stream);
 
 /* Number of kernels this context has launched so far. */
 long long cdcc_kernel_launches(const cdcc_ctx *ctx);

@@ -290,7 +290,41 @@ def cdcc_phase_times(ctx):
     return t
 
 
-KERNEL_CLASSES = ("gemm64", "permute", "update", "contract_dL", "other")
+KERNEL_CLASSES = ("gemm64", "permute", "update", "contract_dL", "other",
+                  "tc_gemm")
+
+
+def cdcc_solver_info(ctx):
+    """(ccsd mixed, ccsd fp64, lambda mixed, lambda fp64) iterations."""
+    lib = load()
+    lib.cdcc_solver_info.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.cdcc_solver_info.restype = ctypes.c_int
+    info = np.zeros(4, dtype=np.int32)
+    _check(ctx, lib.cdcc_solver_info(ctx.handle,
+                                     info.ctypes.data_as(ctypes.c_void_p)))
+    return tuple(int(x) for x in info)
+
+
+def cdcc_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
+               mode=0, stream=None):
+    """C = beta C + alpha op(A) op(B) on CUDA tensors (row-major)."""
+    lib = load()
+    lib.cdcc_dgemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.c_int, ctypes.c_double, ctypes.c_void_p,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
+    lib.cdcc_dgemm.restype = ctypes.c_int
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.cdcc_dgemm(int(transA), int(transB), int(M), int(N), int(K),
+                        float(alpha), ctypes.c_void_p(A.data_ptr()), int(lda),
+                        ctypes.c_void_p(B.data_ptr()), int(ldb), float(beta),
+                        ctypes.c_void_p(C.data_ptr()), int(ldc), int(mode),
+                        ctypes.c_void_p(int(stream)))
+    if st != CDCC_OK:
+        raise CdccError(st, "cdcc_dgemm failed")
 
 
 def cdcc_profile(ctx, enable=True):

@@ -133,6 +133,8 @@ struct cdcc_ctx {
   Tensor *Gam = nullptr, *Gsym = nullptr, *D1a = nullptr, *D1s = nullptr;
   Tensor *Govov = nullptr, *Govvv = nullptr, *W0 = nullptr;
   Diis cc_diis, lam_diis;
+  unsigned int* d_err = nullptr;
+  int iters_mixed[2] = {0, 0}, iters_fp64[2] = {0, 0};
 };
 
 namespace {
@@ -465,25 +467,73 @@ struct PhaseTimer {
   }
 };
 
+// Precision schedule (MIXED): the amplitude-independent integrals and the
+// density sweep use 3-slice tensor-core products; the CCSD and Lambda
+// iterations use 2-slice products until max|R/D| < switch_tol and FP64
+// contractions afterwards, so the converged amplitudes satisfy the FP64
+// equations.
+int mixed(cdcc_ctx* c) { return c->opt.precision == CDCC_PREC_MIXED; }
+
+// Leave the reduced-precision iterations once max|R/D| is below switch_tol,
+// or once it has stopped improving (3 iterations without a 30% gain), which
+// happens when the residual reaches the floor of the reduced precision.
+struct SwitchRule {
+  double tol, best = 1e300;
+  int since = 0;
+  explicit SwitchRule(double t) : tol(t) {}
+  bool done(double r) {
+    if (r < tol) return true;
+    if (r < 0.7 * best) {
+      best = r;
+      since = 0;
+    } else if (++since >= 3) {
+      return true;
+    }
+    return false;
+  }
+};
+
+void check_device_error(cdcc_ctx* c) {
+  unsigned int err = 0;
+  CK(cudaMemcpyAsync(&err, c->d_err, 4, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (err)
+    throw StatusError(CDCC_ETIMEOUT,
+                      "a bounded device wait gave up (code " +
+                          std::to_string(err) + ")");
+}
+
 void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 0);
   e.zero(c->amp);
+  // the amplitude-independent integrals enter every later FP64 iteration, so
+  // they are built with FP64-accurate products
+  e.set_precision(0);
   prepare(c);
+  e.set_precision(mixed(c) ? 2 : 0);
+  SwitchRule sw(c->opt.switch_tol);
   c->tape_ready = false;
+  c->iters_mixed[0] = c->iters_fp64[0] = 0;
   diis_init(c, c->cc_diis, "ccdiis", c->amp->lay.size);
   double e_old = 0, rmax = 0, E = 0;
   bool have_old = false;
   int it = 1;
   for (; it <= c->opt.max_iter; ++it) {
     residual(c);
+    (e.precision() ? c->iters_mixed[0] : c->iters_fp64[0])++;
     E = scalar(c, c->E);
     rmax = probe_step(c, c->R1, c->R2, c->err1);
     if (!std::isfinite(rmax) || !std::isfinite(E))
       throw StatusError(CDCC_ENUMERIC, "non-finite CCSD residual");
-    if (rmax <= c->opt.conv_tol && have_old &&
+    if (e.precision() == 0 && rmax <= c->opt.conv_tol && have_old &&
         std::fabs(E - e_old) <= c->opt.energy_tol)
       break;
+    if (e.precision() && sw.done(rmax)) {
+      e.set_precision(0);   // re-evaluate at the same amplitudes in FP64
+      have_old = false;
+      continue;
+    }
     e_old = E;
     have_old = true;
     e.timed(Engine::K_OTHER, 24.0 * c->amp->lay.size, [&] {
@@ -492,6 +542,7 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
     if (it >= 2) diis_step(c, c->cc_diis, c->amp, c->err1);
   }
   pt.stop();
+  check_device_error(c);
   if (it > c->opt.max_iter)
     throw StatusError(CDCC_ENOCONV, "CCSD did not converge");
   c->e_corr = E - c->e_ref;
@@ -503,11 +554,17 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
 
 void ensure_tape(cdcc_ctx* c) {
   if (c->tape_ready) return;
-  c->eng->clear_tape();
-  c->eng->record(true);
+  Engine& e = *c->eng;
+  e.clear_tape();
+  e.record(true);
+  e.record_only(true);   // the t-independent integrals are already built
   prepare(c);
+  e.record_only(false);
+  const int prec = e.precision();
+  e.set_precision(0);
   residual(c);
-  c->eng->record(false);
+  e.set_precision(prec);
+  e.record(false);
   c->tape_ready = true;
 }
 
@@ -516,25 +573,32 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
   PhaseTimer pt(c, 1);
   ensure_tape(c);
   e.zero(c->lam);
+  e.set_precision(mixed(c) ? 2 : 0);
+  SwitchRule sw(c->opt.switch_tol);
+  c->iters_mixed[1] = c->iters_fp64[1] = 0;
   diis_init(c, c->lam_diis, "lamdiis", c->lam->lay.size);
-  Tensor* g = e.adjoint(c->amp);
   Tensor* g1 = e.adjoint(c->T1);
   Tensor* g2 = e.adjoint(c->T2);
   double rmax = 0;
   int it = 1;
   for (; it <= c->opt.max_iter; ++it) {
     e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}}, TAG_AMP);
+    (e.precision() ? c->iters_mixed[1] : c->iters_fp64[1])++;
     rmax = probe_step(c, g1, g2, c->err1);
     if (!std::isfinite(rmax))
       throw StatusError(CDCC_ENUMERIC, "non-finite Lambda residual");
-    if (rmax <= c->opt.conv_tol) break;
+    if (e.precision() == 0 && rmax <= c->opt.conv_tol) break;
+    if (e.precision() && sw.done(rmax)) {
+      e.set_precision(0);
+      continue;
+    }
     e.timed(Engine::K_OTHER, 24.0 * c->lam->lay.size, [&] {
       return axpby(1.0, c->err1->d, 1.0, c->lam->d, c->lam->lay.size, c->st);
     });
     if (it >= 2) diis_step(c, c->lam_diis, c->lam, c->err1);
   }
-  (void)g;
   pt.stop();
+  check_device_error(c);
   if (it > c->opt.max_iter)
     throw StatusError(CDCC_ENOCONV, "Lambda did not converge");
   if (iters) *iters = it;
@@ -546,8 +610,10 @@ void run_density(cdcc_ctx* c, double* D1) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 2);
   ensure_tape(c);
+  e.set_precision(mixed(c) ? 3 : 0);
   e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}},
              TAG_L | TAG_H);
+  e.set_precision(0);
   // Gamma^P_pq: embed the block adjoints into the packed pattern, symmetrise
   e.zero(c->Gam);
   e.axpy(1.0, e.adjoint(c->Loo), "Pij", 1.0, c->Gam, "Pij");
@@ -826,6 +892,9 @@ void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
   c->d_dots = (double*)e.al.alloc(16 * 8);
   c->partial_n = multi_dot_partial_doubles(na, 16);
   c->d_partial = (double*)e.al.alloc((size_t)c->partial_n * 8);
+  c->d_err = (unsigned int*)e.al.alloc(16);
+  CK(cudaMemsetAsync(c->d_err, 0, 16, c->st));
+  e.d_err = c->d_err;
   CK(cudaStreamSynchronize(c->st));
   c->state = 1;
 }
@@ -863,6 +932,7 @@ void free_ctx(cdcc_ctx* c) {
     e.al.release(c->d_max, 8);
     e.al.release(c->d_dots, 16 * 8);
     e.al.release(c->d_partial, (size_t)c->partial_n * 8);
+    e.al.release(c->d_err, 16);
     cudaStreamSynchronize(c->st);
     c->eng.reset();
   }
@@ -1014,6 +1084,79 @@ cdcc_status cdcc_kernel_stats(cdcc_ctx* c, int kind, double* seconds,
     if (launches) *launches = (long long)c->eng->prof_n[kind];
     if (work) *work = c->eng->prof_work[kind];
   });
+}
+
+cdcc_status cdcc_solver_info(cdcc_ctx* c, int* info) {
+  if (!c || !info) return CDCC_EINVAL;
+  info[0] = c->iters_mixed[0];
+  info[1] = c->iters_fp64[0];
+  info[2] = c->iters_mixed[1];
+  info[3] = c->iters_fp64[1];
+  return CDCC_OK;
+}
+
+cdcc_status cdcc_dgemm(int transA, int transB, int M, int N, int K,
+                       double alpha, const double* A, int lda,
+                       const double* B, int ldb, double beta, double* C,
+                       int ldc, int mode, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || mode < 0 || mode > 3) return CDCC_EINVAL;
+  if (M == 0 || N == 0) return CDCC_OK;
+  if (!A || !B || !C) return CDCC_EINVAL;
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C))
+    return CDCC_EINVAL;
+  const int rowsA = transA ? K : M, colsA = transA ? M : K;
+  const int rowsB = transB ? N : K, colsB = transB ? K : N;
+  if (lda < std::max(1, colsA) || ldb < std::max(1, colsB) || ldc < N)
+    return CDCC_EINVAL;
+  (void)rowsA;
+  (void)rowsB;
+  cudaStream_t st = (cudaStream_t)stream;
+  GemmProb g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.lda = lda;
+  g.ldb = ldb;
+  g.ldc = ldc;
+  g.ta = transA ? 1 : 0;
+  g.tb = transB ? 1 : 0;
+  void* ws = nullptr;
+  double* sk = nullptr;
+  unsigned int* err = nullptr;
+  cdcc_status s = CDCC_OK;
+  try {
+    if (mode == 0) {
+      const int64_t n = gemm_scratch_doubles(&g, 1);
+      if (n > 0) CK(cudaMallocAsync((void**)&sk, (size_t)n * 8, st));
+      gemm64_grouped(&g, 1, alpha, beta, sk, st);
+    } else {
+      const int64_t wb = tc_workspace_bytes(&g, 1, mode);
+      const int64_t n = tc_scratch_doubles(&g, 1, mode);
+      CK(cudaMallocAsync(&ws, (size_t)wb, st));
+      if (n > 0) CK(cudaMallocAsync((void**)&sk, (size_t)n * 8, st));
+      CK(cudaMallocAsync((void**)&err, 16, st));
+      CK(cudaMemsetAsync(err, 0, 16, st));
+      tc_gemm_grouped(&g, 1, alpha, beta, mode, ws, sk, err, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    if (err) {
+      unsigned int h = 0;
+      CK(cudaMemcpy(&h, err, 4, cudaMemcpyDeviceToHost));
+      if (h) s = CDCC_ETIMEOUT;
+    }
+  } catch (const std::exception&) {
+    s = CDCC_ECUDA;
+  }
+  if (ws) cudaFreeAsync(ws, st);
+  if (sk) cudaFreeAsync(sk, st);
+  if (err) cudaFreeAsync(err, st);
+  cudaStreamSynchronize(st);
+  return s;
 }
 
 long long cdcc_kernel_launches(const cdcc_ctx* c) {

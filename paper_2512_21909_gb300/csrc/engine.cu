@@ -342,6 +342,7 @@ void Engine::axpy_raw(double alpha, const Layout& XL, const double* X,
 void Engine::axpy(double alpha, Tensor* X, const char* ix, double beta,
                   Tensor* Y, const char* iy) {
   if (recording_) tape_.push_back({1, alpha, beta, X, nullptr, Y, ix, "", iy});
+  if (record_only_) return;
   axpy_raw(alpha, X->lay, X->d, ix, beta, Y->lay, Y->d, iy);
 }
 
@@ -354,6 +355,7 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
     throw EngineError("contract: index strings " + ia + "," + ib + "->" + ic +
                       " do not match ranks");
   if (recording_) tape_.push_back({0, alpha, beta, A, B, C, ia, ib, ic});
+  if (record_only_) return;
 
   std::string KA, KB, fA_A, fB_B, fA_C, fB_C;
   for (char x : ia) {
@@ -535,14 +537,27 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
     flops += 2 * M * N * K;
     probs[np++] = g;
   }
-  const int64_t sk = gemm_scratch_doubles(probs, np);
-  double* skb = sk > 0 ? scratch(sk) : nullptr;
   double fl = 0;
   for (int i = 0; i < np; ++i)
     fl += 2.0 * probs[i].M * (double)probs[i].N * probs[i].K;
-  timed(K_GEMM64, fl, [&] {
-    return gemm64_grouped(probs, np, alpha, direct ? beta : 0.0, skb, st_);
-  });
+  if (tc_slices_ > 0 && fl >= (double)tc_min_flops && np <= 8 && d_err) {
+    // split-precision tensor-core path
+    const int64_t wsb = tc_workspace_bytes(probs, np, tc_slices_);
+    double* ws = scratch((wsb + 7) / 8);
+    const int64_t sk = tc_scratch_doubles(probs, np, tc_slices_);
+    double* skb = sk > 0 ? scratch(sk) : nullptr;
+    tc_flops += (int64_t)fl;
+    timed(K_TC, fl, [&] {
+      return tc_gemm_grouped(probs, np, alpha, direct ? beta : 0.0,
+                             tc_slices_, ws, skb, d_err, st_);
+    });
+  } else {
+    const int64_t sk = gemm_scratch_doubles(probs, np);
+    double* skb = sk > 0 ? scratch(sk) : nullptr;
+    timed(K_GEMM64, fl, [&] {
+      return gemm64_grouped(probs, np, alpha, direct ? beta : 0.0, skb, st_);
+    });
+  }
   if (!direct)
     axpy_raw(1.0, *DL, Dd, best.X + best.Y, beta, C->lay, C->d, ic);
   release_scratch();

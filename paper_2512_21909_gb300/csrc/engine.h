@@ -91,6 +91,8 @@ class Engine {
 
   // tape
   void record(bool on) { recording_ = on; }
+  // append to the tape without executing (results already in place)
+  void record_only(bool on) { record_only_ = on; }
   void clear_tape() { tape_.clear(); }
   size_t tape_size() const { return tape_.size(); }
   // Run the tape backwards.  `seeds`: (tensor, seed values tensor or null =
@@ -108,9 +110,18 @@ class Engine {
   int64_t launches = 0;
   int64_t flops = 0;  // FP64 GEMM flops issued
 
+  // Arithmetic of the contractions: 0 = FP64 DFMA; 1..3 = tensor-core GEMM
+  // with that many BF16 slices for every contraction of at least
+  // `tc_min_flops` flops (smaller ones stay FP64).
+  void set_precision(int slices) { tc_slices_ = slices; }
+  int precision() const { return tc_slices_; }
+  int64_t tc_min_flops = (int64_t)1 << 26;
+  unsigned int* d_err = nullptr;   // device error flag of bounded waits
+  int64_t tc_flops = 0;            // algorithmic flops run on tensor cores
+
   // Optional per-kernel-class timing with CUDA events on the engine stream.
   enum ProfKind : int { K_GEMM64 = 0, K_PERM = 1, K_UPDATE = 2, K_DOT = 3,
-                        K_OTHER = 4, K_NKIND = 5 };
+                        K_OTHER = 4, K_TC = 5, K_NKIND = 6 };
   void profile(bool on) { prof_on_ = on; }
   template <class F>
   void timed(int kind, double work, F launch) {
@@ -157,6 +168,7 @@ class Engine {
   Dims dims_;
   cudaStream_t st_;
   bool recording_ = false;
+  bool record_only_ = false;
   std::vector<Op> tape_;
   std::map<std::string, std::unique_ptr<Tensor>> tensors_;
   std::map<std::string, DevTasks> task_cache_;
@@ -176,6 +188,7 @@ class Engine {
   };
   cudaEvent_t get_event();
   bool prof_on_ = false;
+  int tc_slices_ = 0;
   std::vector<ProfRec> pending_;
   std::vector<cudaEvent_t> ev_pool_;
 };

@@ -28,6 +28,17 @@ int64_t gemm_scratch_doubles(const GemmProb* p, int np);
 int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
                    double* scratch, cudaStream_t st);
 
+// Split-precision tensor-core GEMM (tc_gemm.cu): same semantics as
+// gemm64_grouped, at most 8 products, nslice BF16 slices per operand (1-3).
+// `workspace` holds tc_workspace_bytes() bytes of BF16 slices, `scratch`
+// tc_scratch_doubles() doubles of split-K partials; *d_err becomes nonzero
+// if a bounded device wait gave up.
+int64_t tc_workspace_bytes(const GemmProb* p, int np, int nslice);
+int64_t tc_scratch_doubles(const GemmProb* p, int np, int nslice);
+int tc_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
+                    int nslice, void* workspace, double* scratch,
+                    unsigned int* d_err, cudaStream_t st);
+
 // Y = beta*Y + alpha*X over the boxes described by tasks/chunks.
 int perm_axpy(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
               double alpha, const double* X, double beta, double* Y,

@@ -1,0 +1,561 @@
+// tc_gemm.cu -- split-precision tensor-core GEMM for sm_103a (tcgen05 + TMA).
+//
+// C (FP64) = beta*C + alpha * op(A) op(B) with FP64 operands, computed on
+// the 5th-generation tensor cores:
+//   * each FP64 operand element is split into s BF16 slices
+//       x = x0 + x1 (+ x2),  x0 = bf16(x), x1 = bf16(x - x0), ...
+//     (residuals formed exactly in FP64), stored K-major;
+//   * the products x_i * y_j with i + j < s (1, 3 or 6 of them) are summed
+//     by tcgen05.mma.kind::f16 into ONE FP32 accumulator in tensor memory;
+//     s = 2 keeps ~16 significant bits per operand ("BF16x3"), s = 3 keeps
+//     ~24 bits (FP32-class products);
+//   * operand tiles are staged by TMA (128B swizzle, OOB rows/cols read as
+//     zero) through a multi-stage mbarrier pipeline; one thread issues the
+//     MMAs, tcgen05.commit frees smem stages; 4 warps drain the accumulator
+//     with tcgen05.ld and write FP64 (split-K partials go to scratch and are
+//     summed in a fixed order).
+// Tile: 128 rows (MMA M = 128, one CTA) x BN in {32, 64, 128} columns; the
+// larger output dimension is mapped to the 128-row side (C is then written
+// transposed).  Every mbarrier wait is bounded; on a timeout the kernel sets
+// an error flag, stops issuing work and still releases its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+
+#include "kernels.h"
+
+namespace cdcc {
+
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;          // K per stage: one 128-byte swizzle row
+constexpr int TC_THREADS = 128;
+constexpr int TC_MAXPROB = 8;
+constexpr int TC_SMEM_BUDGET = 200 * 1024;
+constexpr long long TC_SPIN_LIMIT = 1LL << 22;
+
+struct TcLaunch {
+  CUtensorMap ta[TC_MAXPROB];  // A slices: dims {Kp, rows, s}, box {64,128,1}
+  CUtensorMap tb[TC_MAXPROB];  // B slices: dims {Kp, cols, s}, box {64,BN,1}
+  double* C[TC_MAXPROB];
+  int64_t poff[TC_MAXPROB];
+  int M[TC_MAXPROB], N[TC_MAXPROB], ldc[TC_MAXPROB], nkb[TC_MAXPROB];
+  int tm[TC_MAXPROB], tn[TC_MAXPROB], ks[TC_MAXPROB];
+  int tile0[TC_MAXPROB + 1];
+  int np, nslice, bn, stages, trans_out;
+  double alpha, beta;
+  double* scratch;
+  unsigned int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_u32(b)),
+      "r"(bytes)
+      : "memory");
+}
+
+// Bounded wait on an mbarrier phase; false (and *err = code) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity,
+                                          unsigned int* err,
+                                          unsigned int code) {
+  const uint32_t a = smem_u32(b);
+  for (long long i = 0; i < TC_SPIN_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  atomicExch(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map,
+                                            int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::"
+      "complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups
+// 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused, swizzled)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad,
+                                         uint64_t bd, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+      "[%0];" ::"r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+        "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ TcLaunch L) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int S = L.stages, s = L.nslice, BN = L.bn;
+  const uint32_t a_bytes = TC_BM * 128, b_bytes = (uint32_t)BN * 128;
+  const uint32_t stage_bytes = (uint32_t)s * (a_bytes + b_bytes);
+  uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
+  uint64_t* empty = full + S;
+  uint64_t* done = empty + S;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+
+  const int bid = blockIdx.x;
+  int pi = 0;
+  while (pi + 1 < L.np && bid >= L.tile0[pi + 1]) ++pi;
+  int local = bid - L.tile0[pi];
+  const int ksn = L.ks[pi];
+  const int ksi = local % ksn;
+  local /= ksn;
+  const int tn = local % L.tn[pi];
+  const int tm = local / L.tn[pi];
+  const int m0 = tm * TC_BM, n0 = tn * BN;
+  const int nkb = L.nkb[pi];
+  const int per = (nkb + ksn - 1) / ksn;
+  const int kb0 = ksi * per, kb1 = min(nkb, kb0 + per);
+  const int nit = max(0, kb1 - kb0);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ncols = BN < 32 ? 32 : (uint32_t)BN;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], "
+        "%1;" ::"r"(smem_u32(tmem_slot)),
+        "r"(ncols)
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                         ((uint32_t)(BN >> 3) << 17) |
+                         ((uint32_t)(TC_BM >> 4) << 24);
+
+  if (warp == 0 && lane == 0 && nit > 0) {
+    // ---- TMA producer
+    for (int it = 0; it < nit; ++it) {
+      const int st = it % S, round = it / S;
+      if (round > 0 && !mbar_wait(&empty[st], (round - 1) & 1, L.err, 1))
+        break;
+      mbar_expect_tx(&full[st], stage_bytes);
+      uint8_t* sa = smem + (size_t)st * stage_bytes;
+      uint8_t* sb = sa + (size_t)s * a_bytes;
+      const int kc = (kb0 + it) * TC_BK;
+      for (int i = 0; i < s; ++i) {
+        tma_load_3d(sa + (size_t)i * a_bytes, &L.ta[pi], kc, m0, i, &full[st]);
+        tma_load_3d(sb + (size_t)i * b_bytes, &L.tb[pi], kc, n0, i, &full[st]);
+      }
+    }
+  } else if (warp == 1 && lane == 0 && nit > 0) {
+    // ---- MMA issuer
+    bool ok = true;
+    for (int it = 0; it < nit && ok; ++it) {
+      const int st = it % S, round = it / S;
+      if (!mbar_wait(&full[st], round & 1, L.err, 2)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
+      const uint32_t sb = sa + (uint32_t)s * a_bytes;
+      int first = (it == 0);
+      for (int d = 0; d < s; ++d)          // slice products i + j = d
+        for (int i = 0; i <= d; ++i) {
+          const int j = d - i;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            const uint64_t ad = smem_desc(sa + i * a_bytes + kk * 32);
+            const uint64_t bd = smem_desc(sb + j * b_bytes + kk * 32);
+            mma_bf16(tmem, ad, bd, idesc, first ? 0u : 1u);
+            first = 0;
+          }
+        }
+      mma_commit(&empty[st]);
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  // ---- epilogue: 4 warps x 32 TMEM lanes = 128 rows
+  bool have = nit > 0;
+  if (have) have = mbar_wait(done, 0, L.err, 3);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int r = m0 + warp * 32 + lane;  // row of the 128-row side
+  const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
+  const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
+  double* C = L.C[pi];
+  const int ldc = L.ldc[pi];
+  float v[32];
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    if (have) {
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = 0.f;
+    }
+    if (r >= Mr) continue;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const int cc = n0 + c0 + i;
+      if (cc >= Nc) break;
+      // logical C element (m, n)
+      const int m = L.trans_out ? cc : r, n = L.trans_out ? r : cc;
+      if (ksn == 1) {
+        double* p = C + (int64_t)m * ldc + n;
+        const double val = L.alpha * (double)v[i];
+        *p = (L.beta == 0.0) ? val : fma(L.beta, *p, val);
+      } else {
+        L.scratch[L.poff[pi] + (int64_t)ksi * L.M[pi] * L.N[pi] +
+                  (int64_t)m * L.N[pi] + n] = (double)v[i];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
+                     tmem),
+                 "r"(ncols)
+                 : "memory");
+  }
+}
+
+// FP64 rows -> s BF16 slices, K-major [slice][row][Kp], zero padded in K.
+// src element (row, k) = trans ? src[k*ld + row] : src[row*ld + k]
+__global__ void split_kernel(const double* __restrict__ src, int rows, int K,
+                             int64_t ld, int trans,
+                             __nv_bfloat16* __restrict__ dst, int Kp, int s,
+                             int64_t slice_stride) {
+  const int64_t total = (int64_t)rows * Kp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row, k;
+    if (!trans) {
+      row = e / Kp;
+      k = e % Kp;
+    } else {  // walk rows fastest so that the FP64 reads are coalesced
+      k = e / rows;
+      row = e % rows;
+    }
+    double x = 0.0;
+    if (k < K) x = trans ? src[k * ld + row] : src[row * ld + k];
+    const int64_t o = row * Kp + k;
+    for (int i = 0; i < s; ++i) {
+      const __nv_bfloat16 b = __float2bfloat16_rn((float)x);
+      dst[(int64_t)i * slice_stride + o] = b;
+      x -= (double)__bfloat162float(b);
+    }
+  }
+}
+
+struct ReduceL {
+  double* C[TC_MAXPROB];
+  int M[TC_MAXPROB], N[TC_MAXPROB], ldc[TC_MAXPROB], ks[TC_MAXPROB];
+  int64_t poff[TC_MAXPROB], elem0[TC_MAXPROB + 1];
+  int np;
+  double alpha, beta;
+  const double* scratch;
+};
+
+__global__ void tc_reduce_kernel(const __grid_constant__ ReduceL R) {
+  const int64_t total = R.elem0[R.np];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int pi = 0;
+    while (pi + 1 < R.np && e >= R.elem0[pi + 1]) ++pi;
+    const int64_t loc = e - R.elem0[pi];
+    const int m = (int)(loc / R.N[pi]), n = (int)(loc % R.N[pi]);
+    const int64_t MN = (int64_t)R.M[pi] * R.N[pi];
+    const double* part = R.scratch + R.poff[pi] + loc;
+    double acc = 0.0;
+    for (int k = 0; k < R.ks[pi]; ++k) acc += part[k * MN];
+    double* c = R.C[pi] + (int64_t)m * R.ldc[pi] + n;
+    const double v = R.alpha * acc;
+    *c = (R.beta == 0.0) ? v : fma(R.beta, *c, v);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+void encode_init() {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                       cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    fn = nullptr;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+}
+
+void make_map(CUtensorMap* m, const __nv_bfloat16* base, int Kp, int rows,
+              int s, int box_rows) {
+  std::call_once(g_encode_once, encode_init);
+  if (!g_encode) throw std::runtime_error("cuTensorMapEncodeTiled unavailable");
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)s};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t est[3] = {1, 1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base,
+                        dims, strides, box, est, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw std::runtime_error("cuTensorMapEncodeTiled failed: " +
+                             std::to_string((int)r));
+}
+
+struct TcPlan {
+  bool swap;                     // 128-row side = logical N
+  int bn, stages;
+  int rowsA[TC_MAXPROB], rowsB[TC_MAXPROB], Kp[TC_MAXPROB];
+  int tm[TC_MAXPROB], tn[TC_MAXPROB], ks[TC_MAXPROB], nkb[TC_MAXPROB];
+  int64_t ws_elems;              // BF16 slice workspace
+  int64_t scratch;               // FP64 split-K partials
+};
+
+TcPlan tc_plan(const GemmProb* p, int np, int s) {
+  TcPlan pl;
+  std::memset(&pl, 0, sizeof(pl));
+  int64_t sumM = 0, sumN = 0;
+  for (int i = 0; i < np; ++i) {
+    sumM += p[i].M;
+    sumN += p[i].N;
+  }
+  pl.swap = sumN > sumM;
+  int maxc = 0;
+  for (int i = 0; i < np; ++i)
+    maxc = std::max(maxc, pl.swap ? p[i].M : p[i].N);
+  pl.bn = maxc <= 32 ? 32 : maxc <= 64 ? 64 : 128;
+  const int stage = s * (TC_BM * 128 + pl.bn * 128);
+  pl.stages = std::max(1, std::min(4, TC_SMEM_BUDGET / stage));
+  int64_t tiles = 0;
+  for (int i = 0; i < np; ++i) {
+    const int R = pl.swap ? p[i].N : p[i].M;   // 128-row side
+    const int Cc = pl.swap ? p[i].M : p[i].N;  // BN side
+    pl.rowsA[i] = R;
+    pl.rowsB[i] = Cc;
+    pl.Kp[i] = (p[i].K + 7) / 8 * 8;
+    pl.nkb[i] = (p[i].K + TC_BK - 1) / TC_BK;
+    pl.tm[i] = (R + TC_BM - 1) / TC_BM;
+    pl.tn[i] = (Cc + pl.bn - 1) / pl.bn;
+    tiles += (int64_t)pl.tm[i] * pl.tn[i];
+    pl.ws_elems += (int64_t)s * (R + Cc) * pl.Kp[i];
+  }
+  for (int i = 0; i < np; ++i) {
+    pl.ks[i] = 1;
+    if (tiles < 2 * 152 && pl.nkb[i] >= 8) {
+      int ks = (int)((2 * 152 + tiles - 1) / std::max<int64_t>(tiles, 1));
+      ks = std::min(ks, pl.nkb[i] / 4);
+      pl.ks[i] = std::max(1, std::min(ks, 32));
+    }
+    if (pl.ks[i] > 1)
+      pl.scratch += (int64_t)pl.ks[i] * p[i].M * p[i].N;
+  }
+  return pl;
+}
+
+}  // namespace
+
+int64_t tc_workspace_bytes(const GemmProb* p, int np, int nslice) {
+  const TcPlan pl = tc_plan(p, np, nslice);
+  return pl.ws_elems * 2 + 256 * TC_MAXPROB * 2;
+}
+
+int64_t tc_scratch_doubles(const GemmProb* p, int np, int nslice) {
+  return tc_plan(p, np, nslice).scratch;
+}
+
+int tc_gemm_grouped(const GemmProb* pin, int np_in, double alpha, double beta,
+                    int nslice, void* workspace, double* scratch,
+                    unsigned int* d_err, cudaStream_t st) {
+  GemmProb p[TC_MAXPROB];
+  int np = 0;
+  for (int i = 0; i < np_in; ++i)
+    if (pin[i].M > 0 && pin[i].N > 0) {
+      if (np == TC_MAXPROB) throw std::runtime_error("tc: too many blocks");
+      p[np++] = pin[i];
+    }
+  if (np == 0) return 0;
+  if (nslice < 1 || nslice > 3) throw std::runtime_error("tc: nslice");
+  const TcPlan pl = tc_plan(p, np, nslice);
+  TcLaunch* L = new TcLaunch;
+  std::memset(L, 0, sizeof(TcLaunch));
+  ReduceL R;
+  std::memset(&R, 0, sizeof(R));
+  int launches = 0;
+  __nv_bfloat16* ws = (__nv_bfloat16*)workspace;
+  int64_t off = 0, poff = 0, relem = 0;
+  int tiles = 0, nr = 0;
+  for (int i = 0; i < np; ++i) {
+    const GemmProb& g = p[i];
+    const int Kp = pl.Kp[i];
+    // logical A (M x K) and B^T (N x K), both K-major
+    __nv_bfloat16* As = ws + off;
+    off += (int64_t)nslice * g.M * Kp;
+    off = (off + 127) / 128 * 128;
+    __nv_bfloat16* Bs = ws + off;
+    off += (int64_t)nslice * g.N * Kp;
+    off = (off + 127) / 128 * 128;
+    {
+      const int64_t tot = (int64_t)g.M * Kp;
+      const int blocks = (int)std::max<int64_t>(
+          1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
+      split_kernel<<<blocks, 256, 0, st>>>(g.A, g.M, g.K, g.lda, g.ta, As, Kp,
+                                           nslice, (int64_t)g.M * Kp);
+      const int64_t totb = (int64_t)g.N * Kp;
+      const int blocksb = (int)std::max<int64_t>(
+          1, std::min<int64_t>((totb + 255) / 256, 152 * 16));
+      // B^T(n, k) = op(B)(k, n): stored N x K when tb, else K x N
+      split_kernel<<<blocksb, 256, 0, st>>>(g.B, g.N, g.K, g.ldb, g.tb ? 0 : 1,
+                                            Bs, Kp, nslice,
+                                            (int64_t)g.N * Kp);
+      launches += 2;
+    }
+    const __nv_bfloat16* rowsrc = pl.swap ? Bs : As;
+    const __nv_bfloat16* colsrc = pl.swap ? As : Bs;
+    make_map(&L->ta[i], rowsrc, Kp, pl.rowsA[i], nslice, TC_BM);
+    make_map(&L->tb[i], colsrc, Kp, pl.rowsB[i], nslice, pl.bn);
+    L->C[i] = g.C;
+    L->M[i] = g.M;
+    L->N[i] = g.N;
+    L->ldc[i] = g.ldc;
+    L->nkb[i] = pl.nkb[i];
+    L->tm[i] = pl.tm[i];
+    L->tn[i] = pl.tn[i];
+    L->ks[i] = pl.ks[i];
+    L->tile0[i] = tiles;
+    L->poff[i] = pl.ks[i] > 1 ? poff : 0;
+    tiles += pl.tm[i] * pl.tn[i] * pl.ks[i];
+    if (pl.ks[i] > 1) {
+      R.C[nr] = g.C;
+      R.M[nr] = g.M;
+      R.N[nr] = g.N;
+      R.ldc[nr] = g.ldc;
+      R.ks[nr] = pl.ks[i];
+      R.poff[nr] = poff;
+      R.elem0[nr] = relem;
+      relem += (int64_t)g.M * g.N;
+      poff += (int64_t)pl.ks[i] * g.M * g.N;
+      ++nr;
+    }
+  }
+  L->tile0[np] = tiles;
+  L->np = np;
+  L->nslice = nslice;
+  L->bn = pl.bn;
+  L->stages = pl.stages;
+  L->trans_out = pl.swap ? 1 : 0;
+  L->alpha = alpha;
+  L->beta = beta;
+  L->scratch = scratch;
+  L->err = d_err;
+  const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
+  const int smem = pl.stages * stage + 1024 + 256;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(tc_gemm_kernel,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    attr_set = true;
+  }
+  tc_gemm_kernel<<<tiles, TC_THREADS, smem, st>>>(*L);
+  delete L;
+  ++launches;
+  if (nr > 0) {
+    R.np = nr;
+    R.elem0[nr] = relem;
+    R.alpha = alpha;
+    R.beta = beta;
+    R.scratch = scratch;
+    const int blocks = (int)std::min<int64_t>((relem + 255) / 256, 4096);
+    tc_reduce_kernel<<<std::max(blocks, 1), 256, 0, st>>>(R);
+    ++launches;
+  }
+  return launches;
+}
+
+}  // namespace cdcc
