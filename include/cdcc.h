@@ -61,8 +61,11 @@ typedef enum {
 /* Arithmetic of the dense contractions.                                   */
 typedef enum {
     CDCC_PREC_FP64 = 0,   /* every contraction in FP64 (DFMA)              */
-    CDCC_PREC_MIXED = 1   /* split-precision tensor-core contractions with
+    CDCC_PREC_MIXED = 1,  /* split-precision tensor-core contractions with
                              an FP64 finish (see cdcc_options)             */
+    CDCC_PREC_TC = 2      /* split-precision tensor-core contractions with
+                             an exact-slice tensor-core finish: every
+                             large contraction on the tensor cores         */
 } cdcc_precision;
 
 typedef void *(*cdcc_alloc_fn)(size_t bytes, void *stream, void *user);
@@ -220,6 +223,11 @@ cdcc_status cdcc_solver_info(cdcc_ctx *ctx, int *info);
  *   mode 0      FP64 DFMA GEMM
  *   mode 1..3   tensor-core GEMM with 1..3 BF16 slices per operand
  *               (products of slices i + j < mode, FP32 accumulation)
+ *   mode 12..14 tensor-core GEMM with 2..4 exact integer slices per
+ *               operand (row / column power-of-two scaling, exact FP32
+ *               partial sums drained into double-float accumulators):
+ *               8 + 7(s-1) bits of every element relative to its row or
+ *               column maximum, FP64-class results for s = 4
  * Allocates its temporaries with cudaMallocAsync on `stream` and
  * synchronises the stream before returning.
  */

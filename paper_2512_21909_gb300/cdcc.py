@@ -22,7 +22,7 @@ CDCC_OK, CDCC_EINVAL, CDCC_ENOMEM, CDCC_ENOCONV, CDCC_ENUMERIC, CDCC_ECUDA, \
 STATUS = {0: "CDCC_OK", 1: "CDCC_EINVAL", 2: "CDCC_ENOMEM", 3: "CDCC_ENOCONV",
           4: "CDCC_ENUMERIC", 5: "CDCC_ECUDA", 6: "CDCC_ESTATE",
           7: "CDCC_ETIMEOUT"}
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_TC = 0, 1, 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                             ctypes.c_void_p)

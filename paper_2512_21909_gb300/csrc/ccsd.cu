@@ -472,7 +472,16 @@ struct PhaseTimer {
 // iterations use 2-slice products until max|R/D| < switch_tol and FP64
 // contractions afterwards, so the converged amplitudes satisfy the FP64
 // equations.
-int mixed(cdcc_ctx* c) { return c->opt.precision == CDCC_PREC_MIXED; }
+int mixed(cdcc_ctx* c) {
+  return c->opt.precision == CDCC_PREC_MIXED ||
+         c->opt.precision == CDCC_PREC_TC;
+}
+// arithmetic of the accurate phases: FP64 DFMA, or (CDCC_PREC_TC) the
+// exact-slice tensor-core products with 4 slices
+int exact_prec(cdcc_ctx* c) {
+  return c->opt.precision == CDCC_PREC_TC ? 14 : 0;
+}
+int early_prec(cdcc_ctx* c) { return mixed(c) ? 2 : exact_prec(c); }
 
 // Leave the reduced-precision iterations once max|R/D| is below switch_tol,
 // or once it has stopped improving (3 iterations without a 30% gain), which
@@ -509,9 +518,10 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
   e.zero(c->amp);
   // the amplitude-independent integrals enter every later FP64 iteration, so
   // they are built with FP64-accurate products
-  e.set_precision(0);
+  e.set_precision(exact_prec(c));
   prepare(c);
-  e.set_precision(mixed(c) ? 2 : 0);
+  e.set_precision(early_prec(c));
+  bool early = mixed(c);
   SwitchRule sw(c->opt.switch_tol);
   c->tape_ready = false;
   c->iters_mixed[0] = c->iters_fp64[0] = 0;
@@ -521,16 +531,17 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
   int it = 1;
   for (; it <= c->opt.max_iter; ++it) {
     residual(c);
-    (e.precision() ? c->iters_mixed[0] : c->iters_fp64[0])++;
+    (early ? c->iters_mixed[0] : c->iters_fp64[0])++;
     E = scalar(c, c->E);
     rmax = probe_step(c, c->R1, c->R2, c->err1);
     if (!std::isfinite(rmax) || !std::isfinite(E))
       throw StatusError(CDCC_ENUMERIC, "non-finite CCSD residual");
-    if (e.precision() == 0 && rmax <= c->opt.conv_tol && have_old &&
+    if (!early && rmax <= c->opt.conv_tol && have_old &&
         std::fabs(E - e_old) <= c->opt.energy_tol)
       break;
-    if (e.precision() && sw.done(rmax)) {
-      e.set_precision(0);   // re-evaluate at the same amplitudes in FP64
+    if (early && sw.done(rmax)) {
+      early = false;        // re-evaluate at the same amplitudes, accurately
+      e.set_precision(exact_prec(c));
       have_old = false;
       continue;
     }
@@ -561,7 +572,7 @@ void ensure_tape(cdcc_ctx* c) {
   prepare(c);
   e.record_only(false);
   const int prec = e.precision();
-  e.set_precision(0);
+  e.set_precision(exact_prec(c));
   residual(c);
   e.set_precision(prec);
   e.record(false);
@@ -573,7 +584,8 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
   PhaseTimer pt(c, 1);
   ensure_tape(c);
   e.zero(c->lam);
-  e.set_precision(mixed(c) ? 2 : 0);
+  e.set_precision(early_prec(c));
+  bool early = mixed(c);
   SwitchRule sw(c->opt.switch_tol);
   c->iters_mixed[1] = c->iters_fp64[1] = 0;
   diis_init(c, c->lam_diis, "lamdiis", c->lam->lay.size);
@@ -583,13 +595,14 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
   int it = 1;
   for (; it <= c->opt.max_iter; ++it) {
     e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}}, TAG_AMP);
-    (e.precision() ? c->iters_mixed[1] : c->iters_fp64[1])++;
+    (early ? c->iters_mixed[1] : c->iters_fp64[1])++;
     rmax = probe_step(c, g1, g2, c->err1);
     if (!std::isfinite(rmax))
       throw StatusError(CDCC_ENUMERIC, "non-finite Lambda residual");
-    if (e.precision() == 0 && rmax <= c->opt.conv_tol) break;
-    if (e.precision() && sw.done(rmax)) {
-      e.set_precision(0);
+    if (!early && rmax <= c->opt.conv_tol) break;
+    if (early && sw.done(rmax)) {
+      early = false;
+      e.set_precision(exact_prec(c));
       continue;
     }
     e.timed(Engine::K_OTHER, 24.0 * c->lam->lay.size, [&] {
@@ -610,7 +623,7 @@ void run_density(cdcc_ctx* c, double* D1) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 2);
   ensure_tape(c);
-  e.set_precision(mixed(c) ? 3 : 0);
+  e.set_precision(c->opt.precision == CDCC_PREC_TC ? 14 : (mixed(c) ? 3 : 0));
   e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}},
              TAG_L | TAG_H);
   e.set_precision(0);
@@ -1099,7 +1112,9 @@ cdcc_status cdcc_dgemm(int transA, int transB, int M, int N, int K,
                        double alpha, const double* A, int lda,
                        const double* B, int ldb, double beta, double* C,
                        int ldc, int mode, void* stream) {
-  if (M < 0 || N < 0 || K < 0 || mode < 0 || mode > 3) return CDCC_EINVAL;
+  if (M < 0 || N < 0 || K < 0 || mode < 0 || (mode > 3 && mode < 12) ||
+      mode > 14)
+    return CDCC_EINVAL;
   if (M == 0 || N == 0) return CDCC_OK;
   if (!A || !B || !C) return CDCC_EINVAL;
   if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C))
@@ -1133,6 +1148,12 @@ cdcc_status cdcc_dgemm(int transA, int transB, int M, int N, int K,
       const int64_t n = gemm_scratch_doubles(&g, 1);
       if (n > 0) CK(cudaMallocAsync((void**)&sk, (size_t)n * 8, st));
       gemm64_grouped(&g, 1, alpha, beta, sk, st);
+    } else if (mode >= 12) {
+      const int64_t wb = oz_workspace_bytes(&g, 1, mode - 10);
+      CK(cudaMallocAsync(&ws, (size_t)wb, st));
+      CK(cudaMallocAsync((void**)&err, 16, st));
+      CK(cudaMemsetAsync(err, 0, 16, st));
+      oz_gemm_grouped(&g, 1, alpha, beta, mode - 10, ws, err, st);
     } else {
       const int64_t wb = tc_workspace_bytes(&g, 1, mode);
       const int64_t n = tc_scratch_doubles(&g, 1, mode);

@@ -540,7 +540,18 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   double fl = 0;
   for (int i = 0; i < np; ++i)
     fl += 2.0 * probs[i].M * (double)probs[i].N * probs[i].K;
-  if (tc_slices_ > 0 && fl >= (double)tc_min_flops && np <= 8 && d_err) {
+  if (tc_slices_ >= 12 && fl >= (double)tc_min_flops && np <= 8 && d_err) {
+    // FP64-accurate exact-slice tensor-core path
+    const int ns = tc_slices_ - 10;
+    const int64_t wsb = oz_workspace_bytes(probs, np, ns);
+    double* ws = scratch((wsb + 7) / 8);
+    tc_flops += (int64_t)fl;
+    timed(K_TC, fl, [&] {
+      return oz_gemm_grouped(probs, np, alpha, direct ? beta : 0.0, ns, ws,
+                             d_err, st_);
+    });
+  } else if (tc_slices_ > 0 && tc_slices_ <= 3 && fl >= (double)tc_min_flops &&
+             np <= 8 && d_err) {
     // split-precision tensor-core path
     const int64_t wsb = tc_workspace_bytes(probs, np, tc_slices_);
     double* ws = scratch((wsb + 7) / 8);

@@ -111,8 +111,10 @@ class Engine {
   int64_t flops = 0;  // FP64 GEMM flops issued
 
   // Arithmetic of the contractions: 0 = FP64 DFMA; 1..3 = tensor-core GEMM
-  // with that many BF16 slices for every contraction of at least
-  // `tc_min_flops` flops (smaller ones stay FP64).
+  // with that many BF16 slices (FP32 accumulation); 12..14 = exact-slice
+  // tensor-core GEMM with 2..4 integer slices (FP64-class accuracy); applied
+  // to every contraction of at least `tc_min_flops` flops (smaller ones stay
+  // FP64).
   void set_precision(int slices) { tc_slices_ = slices; }
   int precision() const { return tc_slices_; }
   int64_t tc_min_flops = (int64_t)1 << 26;

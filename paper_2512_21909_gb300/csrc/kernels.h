@@ -39,6 +39,14 @@ int tc_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
                     int nslice, void* workspace, double* scratch,
                     unsigned int* d_err, cudaStream_t st);
 
+// FP64-accurate tensor-core GEMM with exact integer slices (tc_ozaki.cu):
+// nslice in 2..4 (4: 29 bits of every element relative to its row /
+// column maximum).  `workspace` holds oz_workspace_bytes() bytes.
+int64_t oz_workspace_bytes(const GemmProb* p, int np, int nslice);
+int oz_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
+                    int nslice, void* workspace, unsigned int* d_err,
+                    cudaStream_t st);
+
 // Y = beta*Y + alpha*X over the boxes described by tasks/chunks.
 int perm_axpy(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
               double alpha, const double* X, double beta, double* Y,

@@ -1,0 +1,530 @@
+// tc_ozaki.cu -- FP64-accurate GEMM on the BF16 tensor cores (sm_103a).
+//
+// Error-free slicing (in the spirit of the Ozaki scheme):
+//   * every row r of op(A) is scaled by 2^-e_r (max |A[r,:]| < 2^e_r) and
+//     every column c of op(B) by 2^-f_c, then cut into integer slices
+//         A[r,k] = 2^e_r * sum_i A_i[r,k] 2^(-8-7i),
+//     A_0 in [-256, 256] (8 bits), A_i in [-64, 64] (7 bits) for i >= 1;
+//     the integers are exact in BF16.  With s slices 8 + 7(s-1) bits of
+//     every element relative to its row maximum are kept (s = 4: 29 bits).
+//   * C[r,c] = 2^(e_r+f_c) sum_d 2^(-16-7d) P_d,  P_d = sum_{i+j=d} A_i B_j,
+//     products with d < s.  Each P_d accumulates in its own FP32 tensor-
+//     memory accumulator and stays an exact integer below 2^24 for a K chunk
+//     of 192 (|terms| <= 2^16 for d = 0, <= 2^15 + 2^13 per k for d > 0).
+//   * after each chunk four drain warps read the s accumulators (tcgen05.ld)
+//     and add 2^(-16-7d) P_d into a per-thread double-float (hi, lo) FP32
+//     pair with error-free TwoSum, so the only rounding is the final
+//     2^-48-level one.  Two accumulator sets alternate so that the drain of
+//     chunk n overlaps the MMAs of chunk n+1.
+// Operands are staged by TMA (128B swizzle) through a 2-stage pipeline; one
+// thread issues tcgen05.mma.kind::f16.  Tile: 128 rows x 64 columns (the
+// larger output dimension on the 128-row side).  Every mbarrier wait is
+// bounded and sets the error flag on timeout.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <stdexcept>
+#include <string>
+
+#include "kernels.h"
+
+namespace cdcc {
+
+namespace {
+
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64;
+constexpr int OZ_KBLK_PER_CHUNK = 3;        // exact FP32 chunk: 192 of K
+constexpr int OZ_THREADS = 192;             // 6 warps
+constexpr int OZ_MAXPROB = 8;
+constexpr int OZ_MAXS = 4;
+constexpr int OZ_STAGES = 2;
+constexpr long long OZ_SPIN_LIMIT = 1LL << 22;
+
+struct OzLaunch {
+  CUtensorMap ta[OZ_MAXPROB];   // 128-row side slices {Kp, rows, s}
+  CUtensorMap tb[OZ_MAXPROB];   // 64-col side slices {Kp, cols, s}
+  const int* erow[OZ_MAXPROB];  // exponents of the 128-row side
+  const int* ecol[OZ_MAXPROB];  // exponents of the column side
+  double* C[OZ_MAXPROB];
+  int M[OZ_MAXPROB], N[OZ_MAXPROB], ldc[OZ_MAXPROB], nkb[OZ_MAXPROB];
+  int tm[OZ_MAXPROB], tn[OZ_MAXPROB];
+  int tile0[OZ_MAXPROB + 1];
+  int np, nslice, trans_out;
+  double alpha, beta;
+  unsigned int* err;
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)),
+               "r"(n)
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b))
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity,
+                                         unsigned int* err,
+                                         unsigned int code) {
+  const uint32_t a = su32(b);
+  for (long long i = 0; i < OZ_SPIN_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  atomicExch(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma3(void* dst, const CUtensorMap* map,
+                                     int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::"
+      "complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t ad, uint64_t bd,
+                                     uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void ucommit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+      "[%0];" ::"r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+        "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// error-free (hi, lo) += v
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (v - bp);
+  hi = s;
+  lo += e;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+    oz_gemm_kernel(const __grid_constant__ OzLaunch L) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int s = L.nslice;
+  constexpr uint32_t A_BYTES = OZ_BM * 128, B_BYTES = OZ_BN * 128;
+  const uint32_t stage_bytes = (uint32_t)s * (A_BYTES + B_BYTES);
+  uint64_t* full = (uint64_t*)(smem + (size_t)OZ_STAGES * stage_bytes);
+  uint64_t* empty = full + OZ_STAGES;
+  uint64_t* accf = empty + OZ_STAGES;   // [2] accumulator set ready
+  uint64_t* acce = accf + 2;            // [2] accumulator set drained
+  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+
+  const int bid = blockIdx.x;
+  int pi = 0;
+  while (pi + 1 < L.np && bid >= L.tile0[pi + 1]) ++pi;
+  const int local = bid - L.tile0[pi];
+  const int tn = local % L.tn[pi], tm = local / L.tn[pi];
+  const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
+  const int nkb = L.nkb[pi];
+  const int nch = (nkb + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t NCOLS = 512;   // two sets of s (<= 4) x 64 columns
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < OZ_STAGES; ++i) {
+      bar_init(&full[i], 1);
+      bar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bar_init(&accf[i], 1);
+      bar_init(&acce[i], 4);   // one arrive per drain warp
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], "
+        "%1;" ::"r"(su32(tmem_slot)),
+        "r"(NCOLS)
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                         ((uint32_t)(OZ_BN >> 3) << 17) |
+                         ((uint32_t)(OZ_BM >> 4) << 24);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      for (int it = 0; it < nkb; ++it) {
+        const int st = it % OZ_STAGES, round = it / OZ_STAGES;
+        if (round > 0 && !bar_wait(&empty[st], (round - 1) & 1, L.err, 11))
+          break;
+        bar_expect(&full[st], stage_bytes);
+        uint8_t* sa = smem + (size_t)st * stage_bytes;
+        uint8_t* sb = sa + (size_t)s * A_BYTES;
+        for (int i = 0; i < s; ++i) {
+          tma3(sa + (size_t)i * A_BYTES, &L.ta[pi], it * OZ_BK, m0, i,
+               &full[st]);
+          tma3(sb + (size_t)i * B_BYTES, &L.tb[pi], it * OZ_BK, n0, i,
+               &full[st]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: chunk c -> accumulator set c & 1
+      bool ok = true;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int set = c & 1;
+        if (c >= 2 && !bar_wait(&acce[set], ((c >> 1) - 1) & 1, L.err, 12)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int kb0 = c * OZ_KBLK_PER_CHUNK;
+        const int kb1 = min(nkb, kb0 + OZ_KBLK_PER_CHUNK);
+        for (int kb = kb0; kb < kb1; ++kb) {
+          const int st = kb % OZ_STAGES, round = kb / OZ_STAGES;
+          if (!bar_wait(&full[st], round & 1, L.err, 13)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = su32(smem + (size_t)st * stage_bytes);
+          const uint32_t sb = sa + (uint32_t)s * A_BYTES;
+          for (int d = 0; d < s; ++d) {
+            const uint32_t acc_addr = tmem + (uint32_t)((set * s + d) * OZ_BN);
+            int first = (kb == kb0);
+            for (int i = 0; i <= d; ++i) {
+              const int j = d - i;
+#pragma unroll
+              for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+                umma(acc_addr, sdesc(sa + i * A_BYTES + kk * 32),
+                     sdesc(sb + j * B_BYTES + kk * 32), idesc,
+                     first ? 0u : 1u);
+                first = 0;
+              }
+            }
+          }
+          ucommit(&empty[st]);
+        }
+        ucommit(&accf[set]);
+      }
+    }
+  } else {
+    // ---- drain warps 2..5: TMEM sub-partition (warp % 4), 32 rows each
+    const int sub = warp & 3;
+    float hi[OZ_BN], lo[OZ_BN];
+#pragma unroll
+    for (int i = 0; i < OZ_BN; ++i) hi[i] = lo[i] = 0.f;
+    for (int c = 0; c < nch; ++c) {
+      const int set = c & 1;
+      if (!bar_wait(&accf[set], (c >> 1) & 1, L.err, 14)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int d = 0; d < s; ++d) {
+        const float sc = exp2f(-16.0f - 7.0f * d);
+#pragma unroll
+        for (int c0 = 0; c0 < OZ_BN; c0 += 32) {
+          float v[32];
+          tld32(tmem + ((uint32_t)(sub * 32) << 16) +
+                    (uint32_t)((set * s + d) * OZ_BN + c0),
+                v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) two_sum_add(hi[c0 + q], lo[c0 + q],
+                                                   v[q] * sc);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(&acce[set]);
+    }
+    // ---- write: row r of the 128-row side, 64 columns
+    const int r = m0 + sub * 32 + lane;
+    const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
+    const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
+    if (r < Mr) {
+      const int er = L.erow[pi][r];
+      double* C = L.C[pi];
+      const int ldc = L.ldc[pi];
+#pragma unroll
+      for (int q = 0; q < OZ_BN; ++q) {
+        const int cc = n0 + q;
+        if (cc < Nc) {
+          const double val =
+              ldexp((double)hi[q] + (double)lo[q], er + L.ecol[pi][cc]);
+          const int m = L.trans_out ? cc : r, n = L.trans_out ? r : cc;
+          double* p = C + (int64_t)m * ldc + n;
+          const double out = L.alpha * val;
+          *p = (L.beta == 0.0) ? out : fma(L.beta, *p, out);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
+                     tmem),
+                 "r"(NCOLS)
+                 : "memory");
+  }
+}
+
+// exponent e of every row: max_k |x(row,k)| < 2^e (0 for an all-zero row)
+__global__ void oz_rowexp_kernel(const double* __restrict__ src, int rows,
+                                 int K, int64_t ld, int trans,
+                                 int* __restrict__ e) {
+  if (!trans) {  // one warp per row, coalesced along k
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= rows) return;
+    double m = 0.0;
+    for (int k = lane; k < K; k += 32) m = fmax(m, fabs(src[(int64_t)w * ld + k]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) e[w] = (m > 0.0) ? ilogb(m) + 1 : 0;
+  } else {       // one thread per row, coalesced across rows
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    double m = 0.0;
+    for (int k = 0; k < K; ++k) m = fmax(m, fabs(src[(int64_t)k * ld + r]));
+    e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
+  }
+}
+
+// integer slices (see file header), K-major [slice][row][Kp]
+__global__ void oz_split_kernel(const double* __restrict__ src, int rows,
+                                int K, int64_t ld, int trans,
+                                const int* __restrict__ e,
+                                __nv_bfloat16* __restrict__ dst, int Kp, int s,
+                                int64_t slice_stride) {
+  const int64_t total = (int64_t)rows * Kp;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row, k;
+    if (!trans) {
+      row = idx / Kp;
+      k = idx % Kp;
+    } else {
+      k = idx / rows;
+      row = idx % rows;
+    }
+    double x = 0.0;
+    if (k < K) x = trans ? src[k * ld + row] : src[row * ld + k];
+    double y = ldexp(x, 8 - e[row]);            // |y| < 256
+    const int64_t o = row * Kp + k;
+    for (int i = 0; i < s; ++i) {
+      const double q = rint(y);
+      dst[(int64_t)i * slice_stride + o] = __float2bfloat16_rn((float)q);
+      y = (y - q) * 128.0;                      // |y| <= 64
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 oz_encode = nullptr;
+std::once_flag oz_once;
+
+void oz_encode_init() {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                       cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    fn = nullptr;
+  oz_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+}
+
+void oz_map(CUtensorMap* m, const __nv_bfloat16* base, int Kp, int rows, int s,
+            int box_rows) {
+  std::call_once(oz_once, oz_encode_init);
+  if (!oz_encode) throw std::runtime_error("cuTensorMapEncodeTiled missing");
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)s};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t est[3] = {1, 1, 1};
+  CUresult r = oz_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base,
+                         dims, strides, box, est,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw std::runtime_error("cuTensorMapEncodeTiled failed: " +
+                             std::to_string((int)r));
+}
+
+bool oz_swap(const GemmProb* p, int np) {
+  int64_t sm = 0, sn = 0;
+  for (int i = 0; i < np; ++i) {
+    sm += p[i].M;
+    sn += p[i].N;
+  }
+  return sn > sm;
+}
+
+}  // namespace
+
+int64_t oz_workspace_bytes(const GemmProb* p, int np, int nslice) {
+  int64_t b = 0;
+  for (int i = 0; i < np; ++i) {
+    if (p[i].M <= 0 || p[i].N <= 0) continue;
+    const int64_t Kp = (p[i].K + 7) / 8 * 8;
+    // four regions per block, each rounded up to 1 KiB
+    b += (int64_t)nslice * (p[i].M + p[i].N) * Kp * 2;
+    b += (int64_t)(p[i].M + p[i].N) * 4 + 4 * 1024;
+  }
+  return b + 1024;
+}
+
+int oz_gemm_grouped(const GemmProb* pin, int np_in, double alpha, double beta,
+                    int nslice, void* workspace, unsigned int* d_err,
+                    cudaStream_t st) {
+  GemmProb p[OZ_MAXPROB];
+  int np = 0;
+  for (int i = 0; i < np_in; ++i)
+    if (pin[i].M > 0 && pin[i].N > 0) {
+      if (np == OZ_MAXPROB) throw std::runtime_error("oz: too many blocks");
+      p[np++] = pin[i];
+    }
+  if (np == 0) return 0;
+  if (nslice < 2 || nslice > OZ_MAXS) throw std::runtime_error("oz: nslice");
+  const bool swap = oz_swap(p, np);
+  OzLaunch* L = new OzLaunch;
+  std::memset(L, 0, sizeof(OzLaunch));
+  uint8_t* ws = (uint8_t*)workspace;
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    uint8_t* q = ws + off;
+    off += (bytes + 1023) / 1024 * 1024;
+    return q;
+  };
+  int launches = 0, tiles = 0;
+  for (int i = 0; i < np; ++i) {
+    const GemmProb& g = p[i];
+    const int Kp = (g.K + 7) / 8 * 8;
+    __nv_bfloat16* As = (__nv_bfloat16*)take((int64_t)nslice * g.M * Kp * 2);
+    __nv_bfloat16* Bs = (__nv_bfloat16*)take((int64_t)nslice * g.N * Kp * 2);
+    int* ea = (int*)take((int64_t)g.M * 4);
+    int* eb = (int*)take((int64_t)g.N * 4);
+    // op(A) rows: A[m][k] (ta = 0) or A stored [k][m];  B^T rows: B stored
+    // [n][k] (tb) or [k][n]
+    const int btr = g.tb ? 0 : 1;
+    if (!g.ta)
+      oz_rowexp_kernel<<<(g.M * 32 + 255) / 256, 256, 0, st>>>(g.A, g.M, g.K,
+                                                               g.lda, 0, ea);
+    else
+      oz_rowexp_kernel<<<(g.M + 255) / 256, 256, 0, st>>>(g.A, g.M, g.K,
+                                                          g.lda, 1, ea);
+    if (!btr)
+      oz_rowexp_kernel<<<(g.N * 32 + 255) / 256, 256, 0, st>>>(g.B, g.N, g.K,
+                                                               g.ldb, 0, eb);
+    else
+      oz_rowexp_kernel<<<(g.N + 255) / 256, 256, 0, st>>>(g.B, g.N, g.K,
+                                                          g.ldb, 1, eb);
+    const int64_t ta_ = (int64_t)g.M * Kp, tb_ = (int64_t)g.N * Kp;
+    const int bla = (int)std::max<int64_t>(
+        1, std::min<int64_t>((ta_ + 255) / 256, 152 * 16));
+    const int blb = (int)std::max<int64_t>(
+        1, std::min<int64_t>((tb_ + 255) / 256, 152 * 16));
+    oz_split_kernel<<<bla, 256, 0, st>>>(g.A, g.M, g.K, g.lda, g.ta, ea, As,
+                                         Kp, nslice, ta_);
+    oz_split_kernel<<<blb, 256, 0, st>>>(g.B, g.N, g.K, g.ldb, btr, eb, Bs,
+                                         Kp, nslice, tb_);
+    launches += 4;
+    const int R = swap ? g.N : g.M, Cc = swap ? g.M : g.N;
+    oz_map(&L->ta[i], swap ? Bs : As, Kp, R, nslice, OZ_BM);
+    oz_map(&L->tb[i], swap ? As : Bs, Kp, Cc, nslice, OZ_BN);
+    L->erow[i] = swap ? eb : ea;
+    L->ecol[i] = swap ? ea : eb;
+    L->C[i] = g.C;
+    L->M[i] = g.M;
+    L->N[i] = g.N;
+    L->ldc[i] = g.ldc;
+    L->nkb[i] = (g.K + OZ_BK - 1) / OZ_BK;
+    L->tm[i] = (R + OZ_BM - 1) / OZ_BM;
+    L->tn[i] = (Cc + OZ_BN - 1) / OZ_BN;
+    L->tile0[i] = tiles;
+    tiles += L->tm[i] * L->tn[i];
+  }
+  L->tile0[np] = tiles;
+  L->np = np;
+  L->nslice = nslice;
+  L->trans_out = swap ? 1 : 0;
+  L->alpha = alpha;
+  L->beta = beta;
+  L->err = d_err;
+  const int stage = nslice * (OZ_BM * 128 + OZ_BN * 128);
+  const int smem = OZ_STAGES * stage + 1024 + 256;
+  cudaFuncSetAttribute(oz_gemm_kernel,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  oz_gemm_kernel<<<tiles, OZ_THREADS, smem, st>>>(*L);
+  delete L;
+  return launches + 1;
+}
+
+}  // namespace cdcc

@@ -60,6 +60,16 @@ def test_dgemm_all_modes(cd, M, N, K, ta, tb):
         torch.cuda.synchronize()
         err = np.abs(dC.cpu().numpy() - ref).max() / bound
         assert err <= BOUND[mode], (mode, err)
+    # exact-slice modes: per element, relative to K * rowmax(A) * colmax(B)
+    scale = 1.5 * K * np.abs(opA).max(axis=1)[:, None] * \
+        np.abs(opB).max(axis=0)[None, :] + 1e-300
+    for mode, bits in ((12, 15), (13, 22), (14, 29)):
+        dC = torch.as_tensor(C0, device="cuda")
+        cd.cdcc_dgemm(ta, tb, M, N, K, 1.5, dA, A.shape[1], dB, B.shape[1],
+                      0.5, dC, N, mode=mode)
+        torch.cuda.synchronize()
+        err = (np.abs(dC.cpu().numpy() - ref) / scale).max()
+        assert err <= 2.0 ** (1 - bits), (mode, err)
 
 
 def _oracle_values(s, dL):
@@ -70,9 +80,9 @@ def _oracle_values(s, dL):
     return r["cc"]["E_corr"], dL @ pack_dense(s, r["G"].numpy())
 
 
-def _mixed(cd, s, dL):
+def _mixed(cd, s, dL, prec=None):
     o = cd.cdcc_default_options()
-    o.precision = cd.PREC_MIXED
+    o.precision = cd.PREC_MIXED if prec is None else prec
     o.conv_tol = 1e-10
     ctx = cd.init_from_system(s, options=o)
     ctx_e, g = cd.gradient(ctx, dL)
@@ -109,3 +119,26 @@ def test_mixed_c1_meets_target(cd):
     e, g, info = _mixed(cd, s, dL)
     assert abs(e - gold["e_corr"]) <= 1e-8
     assert np.abs(g - np.array(gold["gradient"])).max() <= 1e-6
+
+
+@pytest.mark.parametrize("which", ["c0", "ragged", "c1"])
+def test_tensor_core_finish_meets_target(cd, which):
+    """CDCC_PREC_TC: every large contraction on the tensor cores (2-slice
+    early iterations, exact-slice finish, prepare and density)."""
+    if which == "c0":
+        s = make_system(0)
+        dL = make_displacements(s)
+        e_ref, g_ref = _oracle_values(s, dL)
+    elif which == "ragged":
+        s = random_system([3, 2, 2, 1], [30, 22, 18, 14], [70, 60, 56, 50],
+                          seed=303, scale=0.3)
+        dL = make_displacements(s, 4)
+        e_ref, g_ref = _oracle_values(s, dL)
+    else:
+        s = make_system(1)
+        dL = make_displacements(s)
+        gold = json.load(open(os.path.join(HERE, "golden", "c1.json")))
+        e_ref, g_ref = gold["e_corr"], np.array(gold["gradient"])
+    e, g, info = _mixed(cd, s, dL, prec=cd.PREC_TC)
+    assert abs(e - e_ref) <= 1e-8, abs(e - e_ref)
+    assert np.abs(g - g_ref).max() <= 1e-6
