@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", type=int, default=1)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64",
+                    choices=["fp64", "mixed", "tc"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -220,8 +221,8 @@ def run_ours(args, rank, ws):
     def options():
         o = cdcc.cdcc_default_options()
         o.device = dev
-        o.precision = cdcc.PREC_MIXED if args.precision == "mixed" \
-            else cdcc.PREC_FP64
+        o.precision = {"fp64": cdcc.PREC_FP64, "mixed": cdcc.PREC_MIXED,
+                       "tc": cdcc.PREC_TC}[args.precision]
         return o
 
     def one(Lsrc, dLsrc, profile=False):
@@ -267,30 +268,31 @@ def run_ours(args, rank, ws):
     t50 = allmax(float(np.median(times)), ws)
     t99 = allmax(float(np.percentile(times, 99)), ws)
 
-    # ---- the other precision on the same workload (mixed vs FP64 GPU)
-    other = "mixed" if args.precision == "fp64" else "fp64"
+    # ---- the other schedules on the same workload (mixed / TC vs FP64 GPU)
     saved = args.precision
-    args.precision = other
-    one(L_d, dL_d)                       # warm-up of the other schedule
-    o_times, o_e, o_g, o_info = [], None, None, None
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.fill_(1.0)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        o_e, o_g, _, o_stats, _ = one(L_d, dL_d, profile=True)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        o_times.append(ev0.elapsed_time(ev1) * 1e-3)
+    other_lines = []
+    for other in [p for p in ("fp64", "mixed", "tc") if p != saved]:
+        args.precision = other
+        one(L_d, dL_d)                   # warm-up of the other schedule
+        o_times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.fill_(1.0)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            o_e, o_g, _, o_stats, _ = one(L_d, dL_d, profile=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            o_times.append(ev0.elapsed_time(ev1) * 1e-3)
+        tc = o_stats[5]
+        other_lines.append({
+            "precision": other,
+            "time_to_gradient_s": float(np.median(o_times)),
+            "abs_dE_vs_this_run": abs(o_e - e),
+            "max_abs_dg_vs_this_run": float(np.abs(o_g - g).max()),
+            "tc_gemm_s": tc[0],
+            "tc_gemm_tflops": tc[2] / tc[0] / 1e12 if tc[0] > 0 else None})
     args.precision = saved
-    other_line = {"precision": other,
-                  "time_to_gradient_s": float(np.median(o_times)),
-                  "abs_dE_vs_this_run": abs(o_e - e),
-                  "max_abs_dg_vs_this_run": float(np.abs(o_g - g).max()),
-                  "tc_gemm_s": o_stats[5][0] if o_stats else None,
-                  "tc_gemm_tflops": (o_stats[5][2] / o_stats[5][0] / 1e12
-                                     if o_stats and o_stats[5][0] > 0
-                                     else None)}
 
     # ---- end to end through the C ABI with host buffers
     e2e = []
@@ -346,7 +348,7 @@ def run_ours(args, rank, ws):
                      "peak_source": "nominal GB300 FP64 from the profiling "
                                     "recipe (not in MEASURED_PEAKS.json)",
                      "traffic": None},
-        "other_precision": other_line,
+        "other_precisions": other_lines,
         "e2e": {"value": e2e50, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,

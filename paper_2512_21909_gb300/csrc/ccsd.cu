@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -192,6 +193,9 @@ void prepare(cdcc_ctx* c) {
   e.contract(1.0, c->Lov, "Pmc", c->Lvv, "Pbd", 0.0, c->Govvv, "mcbd");
   c->W0 = e.tensor("W0", {SV, SV, SV, SV}, 2);
   e.contract(1.0, c->Lvv, "Pac", c->Lvv, "Pbd", 0.0, c->W0, "abcd");
+  // (ia|jb) and W0[(ab),(cd)] = (ac|bd) are symmetric matrices per block
+  c->Govov->symmetric = c->W0->symmetric = true;
+  c->Govov->constant = c->Govvv->constant = c->W0->constant = true;
 }
 
 // ------------------------------------------------------------------ residual
@@ -833,6 +837,8 @@ void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
   e.axpy(1.0, c->Lpk, "Ppq", 0.0, c->Lvo, "Ppq");
   e.axpy(1.0, c->Lpk, "Ppq", 0.0, c->Lvv, "Ppq");
   c->Loo->tag = c->Lov->tag = c->Lvo->tag = c->Lvv->tag = TAG_L;
+  c->Loo->constant = c->Lov->constant = c->Lvo->constant =
+      c->Lvv->constant = true;
 
   // identity on the occupied space
   c->Ioo = e.tensor("Ioo", {SO, SO}, 1);
@@ -946,6 +952,8 @@ void free_ctx(cdcc_ctx* c) {
     e.al.release(c->d_dots, 16 * 8);
     e.al.release(c->d_partial, (size_t)c->partial_n * 8);
     e.al.release(c->d_err, 16);
+    // optional per-contraction trace of the profiled work of this context
+    if (const char* f = std::getenv("CDCC_TRACE")) e.write_trace(f);
     cudaStreamSynchronize(c->st);
     c->eng.reset();
   }

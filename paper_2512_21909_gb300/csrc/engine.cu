@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <cstdio>
 #include <sstream>
 
 namespace cdcc {
@@ -56,6 +57,10 @@ Engine::~Engine() {
     al.release(kv.second.chunks, kv.second.nchunk * sizeof(Chunk));
   }
   for (auto& b : pool_) al.release(b.d, (size_t)b.n * 8);
+  for (auto& kv : slice_cache_) {
+    al.release(kv.second.data, kv.second.bytes);
+    if (kv.second.exps) al.release(kv.second.exps, kv.second.ebytes);
+  }
   cudaStreamSynchronize(st_);
   for (auto& r : pending_) {
     cudaEventDestroy(r.a);
@@ -182,9 +187,21 @@ void Engine::prof_collect() {
     ev_pool_.push_back(r.b);
   }
   pending_.clear();
+  for (auto& r : trace_pending_) {
+    float ms = 0;
+    ECK(cudaEventElapsedTime(&ms, r.a, r.b));
+    TraceAgg& a = trace_[r.key];
+    a.sec += ms * 1e-3;
+    a.flops += r.flops;
+    a.calls += 1;
+    ev_pool_.push_back(r.a);
+    ev_pool_.push_back(r.b);
+  }
+  trace_pending_.clear();
 }
 
 void Engine::zero(Tensor* t) {
+  ++t->ver;
   if (t->lay.size > 0)
     ECK(cudaMemsetAsync(t->d, 0, (size_t)t->lay.size * 8, st_));
 }
@@ -343,6 +360,7 @@ void Engine::axpy(double alpha, Tensor* X, const char* ix, double beta,
                   Tensor* Y, const char* iy) {
   if (recording_) tape_.push_back({1, alpha, beta, X, nullptr, Y, ix, "", iy});
   if (record_only_) return;
+  ++Y->ver;
   axpy_raw(alpha, X->lay, X->d, ix, beta, Y->lay, Y->d, iy);
 }
 
@@ -356,6 +374,12 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
                       " do not match ranks");
   if (recording_) tape_.push_back({0, alpha, beta, A, B, C, ia, ib, ic});
   if (record_only_) return;
+  ++C->ver;
+  cudaEvent_t tr_a = nullptr;
+  if (prof_on_) {
+    tr_a = get_event();
+    cudaEventRecord(tr_a, st_);
+  }
 
   std::string KA, KB, fA_A, fB_B, fA_C, fB_C;
   for (char x : ia) {
@@ -447,7 +471,7 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   auto get = [&](Tensor* T, const std::string& tl, const std::string& r,
                  const std::string& c) -> Mat {
     bool tr;
-    if (matches(T, tl, r, c, tr)) return {T->d, &T->lay, tr};
+    if (matches(T, tl, r, c, tr)) return {T->d, &T->lay, tr, T};
     std::vector<int> sp;
     for (char x : r + c) sp.push_back(space_of(x));
     tmp_layouts_.push_back(std::make_unique<Layout>(
@@ -455,7 +479,7 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
     const Layout* L = tmp_layouts_.back().get();
     double* buf = scratch(L->size);
     axpy_raw(1.0, T->lay, T->d, tl, 0.0, *L, buf, r + c);
-    return {buf, L, false};
+    return {buf, L, false, nullptr};
   };
   Mat mp = get(P, pl, best.X, best.K);
   Mat mq = get(Q, ql, best.K, best.Y);
@@ -540,29 +564,21 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   double fl = 0;
   for (int i = 0; i < np; ++i)
     fl += 2.0 * probs[i].M * (double)probs[i].N * probs[i].K;
-  if (tc_slices_ >= 12 && fl >= (double)tc_min_flops && np <= 8 && d_err) {
-    // FP64-accurate exact-slice tensor-core path
-    const int ns = tc_slices_ - 10;
-    const int64_t wsb = oz_workspace_bytes(probs, np, ns);
-    double* ws = scratch((wsb + 7) / 8);
-    tc_flops += (int64_t)fl;
-    timed(K_TC, fl, [&] {
-      return oz_gemm_grouped(probs, np, alpha, direct ? beta : 0.0, ns, ws,
-                             d_err, st_);
-    });
-  } else if (tc_slices_ > 0 && tc_slices_ <= 3 && fl >= (double)tc_min_flops &&
-             np <= 8 && d_err) {
-    // split-precision tensor-core path
-    const int64_t wsb = tc_workspace_bytes(probs, np, tc_slices_);
-    double* ws = scratch((wsb + 7) / 8);
-    const int64_t sk = tc_scratch_doubles(probs, np, tc_slices_);
-    double* skb = sk > 0 ? scratch(sk) : nullptr;
-    tc_flops += (int64_t)fl;
-    timed(K_TC, fl, [&] {
-      return tc_gemm_grouped(probs, np, alpha, direct ? beta : 0.0,
-                             tc_slices_, ws, skb, d_err, st_);
-    });
+  // tensor cores only for matrix-shaped blocks: thin products (dots, outer
+  // products, o x o results) stay on the FP64 path with split K
+  double fl_tc = 0;
+  for (int i = 0; i < np; ++i) {
+    const GemmProb& g = probs[i];
+    if (std::min(g.M, g.N) >= 32 && std::max(g.M, g.N) >= 128 && g.K >= 128)
+      fl_tc += 2.0 * g.M * (double)g.N * g.K;
+  }
+  const char* path;
+  if (tc_slices_ > 0 && fl >= (double)tc_min_flops && fl_tc >= 0.9 * fl &&
+      np <= 8 && d_err) {
+    path = tc_slices_ >= 12 ? "exact" : "split";
+    tc_contract(probs, np, mp, mq, alpha, direct ? beta : 0.0, fl);
   } else {
+    path = "fp64";
     const int64_t sk = gemm_scratch_doubles(probs, np);
     double* skb = sk > 0 ? scratch(sk) : nullptr;
     timed(K_GEMM64, fl, [&] {
@@ -571,8 +587,127 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   }
   if (!direct)
     axpy_raw(1.0, *DL, Dd, best.X + best.Y, beta, C->lay, C->d, ic);
+  if (tr_a) {
+    cudaEvent_t tr_b = get_event();
+    cudaEventRecord(tr_b, st_);
+    std::ostringstream key;
+    key << ia << ',' << ib << "->" << ic << " [" << path << ']';
+    trace_pending_.push_back({key.str(), tr_a, tr_b, fl});
+  }
   release_scratch();
   tmp_layouts_.clear();
+}
+
+void Engine::write_trace(const char* file) {
+  prof_collect();
+  FILE* f = std::fopen(file, "a");
+  if (!f) return;
+  std::vector<std::pair<double, std::string>> v;
+  double tot = 0;
+  for (auto& kv : trace_) {
+    v.push_back({kv.second.sec, kv.first});
+    tot += kv.second.sec;
+  }
+  std::sort(v.rbegin(), v.rend());
+  std::fprintf(f, "# contraction trace: %.6f s in %zu signatures\n", tot,
+               v.size());
+  for (auto& p : v) {
+    const TraceAgg& a = trace_[p.second];
+    std::fprintf(f, "%10.6f s %7lld calls %9.3f TFLOP/s  %s\n", a.sec,
+                 (long long)a.calls, a.sec > 0 ? a.flops / a.sec / 1e12 : 0.0,
+                 p.second.c_str());
+  }
+  std::fclose(f);
+}
+
+SlicedOp Engine::slice_side(Tensor* src, const double* ptr, int rows, int K,
+                            int64_t ld, int trans, int nslice, bool exact,
+                            uint8_t** cursor) {
+  const int Kp = slice_kp(K);
+  const size_t bytes = (size_t)nslice * rows * Kp * 2;
+  const size_t ebytes = exact ? (size_t)rows * 4 : 0;
+  auto split = [&](void* d, int* e) {
+    timed(K_OTHER, 8.0 * rows * K + 2.0 * nslice * rows * Kp, [&] {
+      return exact ? split_exact(ptr, rows, K, ld, trans, nslice, d, e, st_)
+                   : split_float(ptr, rows, K, ld, trans, nslice, d, st_);
+    });
+  };
+  if (src && src->constant) {
+    std::ostringstream key;
+    key << (const void*)ptr << ':' << rows << ':' << K << ':' << ld << ':'
+        << trans << ':' << nslice << ':' << (exact ? 'x' : 'f');
+    auto it = slice_cache_.find(key.str());
+    if (it != slice_cache_.end() && it->second.ver == src->ver)
+      return {it->second.data, it->second.exps, rows, Kp};
+    if (it != slice_cache_.end()) {
+      al.release(it->second.data, it->second.bytes);
+      if (it->second.exps) al.release(it->second.exps, it->second.ebytes);
+      slice_cache_.erase(it);
+    }
+    SliceEntry en;
+    en.bytes = bytes;
+    en.ebytes = ebytes;
+    en.ver = src->ver;
+    en.data = al.alloc(bytes);
+    en.exps = exact ? (int*)al.alloc(ebytes) : nullptr;
+    split(en.data, en.exps);
+    slice_cache_[key.str()] = en;
+    return {en.data, en.exps, rows, Kp};
+  }
+  uint8_t* d = *cursor;
+  *cursor += (bytes + 1023) / 1024 * 1024;
+  int* e = nullptr;
+  if (exact) {
+    e = (int*)*cursor;
+    *cursor += (ebytes + 1023) / 1024 * 1024;
+  }
+  split(d, e);
+  return {d, e, rows, Kp};
+}
+
+// Tensor-core contraction: each side is sliced once (constant tensors from
+// the cache), symmetric blocks are read untransposed, then one grouped
+// launch of the split-precision (1-3 slices) or exact-slice (12-14) kernel.
+void Engine::tc_contract(const GemmProb* probs, int np, const Mat& mp,
+                         const Mat& mq, double alpha, double beta, double fl) {
+  const bool exact = tc_slices_ >= 12;
+  const int ns = exact ? tc_slices_ - 10 : tc_slices_;
+  int64_t wsb = 1024;
+  for (int i = 0; i < np; ++i) {
+    const int64_t Kp = slice_kp(probs[i].K);
+    wsb += (int64_t)ns * (probs[i].M + probs[i].N) * Kp * 2 +
+           (int64_t)(probs[i].M + probs[i].N) * 4 + 4 * 1024;
+  }
+  uint8_t* cur = (uint8_t*)scratch((wsb + 7) / 8);
+  TcProb tp[GEMM_MAXPROB];
+  for (int i = 0; i < np; ++i) {
+    const GemmProb& g = probs[i];
+    // op(A) rows: A[m][k] unless ta; symmetric square blocks: A^T == A
+    int ta = g.ta;
+    if (ta && mp.src && mp.src->symmetric && g.M == g.K) ta = 0;
+    // op(B)^T rows: B[n][k] when tb, else B[k][n]
+    int btr = g.tb ? 0 : 1;
+    if (btr && mq.src && mq.src->symmetric && g.N == g.K) btr = 0;
+    tp[i].a = slice_side(mp.src, g.A, g.M, g.K, g.lda, ta, ns, exact, &cur);
+    tp[i].b = slice_side(mq.src, g.B, g.N, g.K, g.ldb, btr, ns, exact, &cur);
+    tp[i].C = g.C;
+    tp[i].M = g.M;
+    tp[i].N = g.N;
+    tp[i].K = g.K;
+    tp[i].ldc = g.ldc;
+  }
+  tc_flops += (int64_t)fl;
+  if (exact) {
+    timed(K_TC, fl, [&] {
+      return oz_gemm_sliced(tp, np, alpha, beta, ns, d_err, st_);
+    });
+  } else {
+    const int64_t sk = tc_sliced_scratch_doubles(tp, np, ns);
+    double* skb = sk > 0 ? scratch(sk) : nullptr;
+    timed(K_TC, fl, [&] {
+      return tc_gemm_sliced(tp, np, alpha, beta, ns, skb, d_err, st_);
+    });
+  }
 }
 
 void Engine::backward(const std::vector<std::pair<Tensor*, Tensor*>>& seeds,

@@ -47,6 +47,12 @@ struct Tensor {
   int tag = TAG_NONE;        // leaf tag (0 = not a leaf)
   Tensor* adj = nullptr;
   bool req = false;
+  // every block is a square symmetric matrix (rows and columns are the same
+  // index group), so it can be read as its own transpose
+  bool symmetric = false;
+  // amplitude independent: its tensor-core slices are cached per version
+  bool constant = false;
+  uint64_t ver = 0;   // bumped on every write
 };
 
 struct DevTasks {
@@ -140,6 +146,8 @@ class Engine {
     if (pending_.size() > 8192) prof_collect();
   }
   void prof_collect();
+  // append the per-contraction trace (profiling on) to `file`
+  void write_trace(const char* file);
   double prof_sec[K_NKIND] = {}, prof_work[K_NKIND] = {};
   int64_t prof_n[K_NKIND] = {};
 
@@ -156,7 +164,34 @@ class Engine {
     double* d;
     const Layout* lay;
     bool trans;
+    Tensor* src;   // the tensor itself when used in place, else null
   };
+  struct SliceEntry {
+    void* data;
+    int* exps;
+    size_t bytes, ebytes;
+    uint64_t ver;
+  };
+  std::map<std::string, SliceEntry> slice_cache_;
+  // contraction trace (profiling on): signature -> events
+  struct TraceRec {
+    std::string key;
+    cudaEvent_t a, b;
+    double flops;
+  };
+  std::vector<TraceRec> trace_pending_;
+  struct TraceAgg {
+    double sec = 0, flops = 0;
+    int64_t calls = 0;
+  };
+  std::map<std::string, TraceAgg> trace_;
+  // K-major slices of one GEMM side (see kernels.h); cached for constant
+  // tensors, else split into the workspace at *cursor
+  SlicedOp slice_side(Tensor* src, const double* ptr, int rows, int K,
+                      int64_t ld, int trans, int nslice, bool exact,
+                      uint8_t** cursor);
+  void tc_contract(const GemmProb* probs, int np, const Mat& mp,
+                   const Mat& mq, double alpha, double beta, double fl);
 
   Tensor* new_tensor(const std::string& name, std::vector<int> spaces,
                      int split, int gtot);

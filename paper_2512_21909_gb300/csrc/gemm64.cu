@@ -233,14 +233,117 @@ void launch_tile(const GemmLaunch& L, int tiles, cudaStream_t st) {
   gemm64_kernel<BM, BN><<<tiles, NT, 0, st>>>(L);
 }
 
+// Tiny outputs with long K (dot products, o x o results): every CTA owns a
+// K chunk and computes the partial sums of all M*N outputs (threads stride
+// over k, block reduction per output); partials are summed in a fixed order.
+bool is_thin(const GemmProb& g) {
+  return g.M > 0 && g.N > 0 && (int64_t)g.M * g.N <= 256 && g.K >= 2048;
+}
+
+int64_t thin_chunk(const GemmProb& g) {
+  return std::max<int64_t>(4096, (g.K + 4 * SMS - 1) / (4 * SMS));
+}
+
+int thin_blocks(const GemmProb& g) {
+  const int64_t kc = thin_chunk(g);
+  return (int)((g.K + kc - 1) / kc);
+}
+
+__global__ void __launch_bounds__(256)
+    thin_kernel(const GemmProb P, int64_t kc, double* __restrict__ part) {
+  __shared__ double red[8];
+  const int64_t k0 = (int64_t)blockIdx.x * kc;
+  const int64_t k1 = min((int64_t)P.K, k0 + kc);
+  for (int o = 0; o < P.M * P.N; ++o) {
+    const int m = o / P.N, n = o % P.N;
+    double acc = 0.0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+      const double a = P.ta ? P.A[k * P.lda + m] : P.A[(int64_t)m * P.lda + k];
+      const double b = P.tb ? P.B[(int64_t)n * P.ldb + k] : P.B[k * P.ldb + n];
+      acc = fma(a, b, acc);
+    }
+    for (int s = 16; s > 0; s >>= 1)
+      acc += __shfl_down_sync(0xffffffffu, acc, s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      part[((int64_t)blockIdx.x * P.M + m) * P.N + n] = t;
+    }
+    __syncthreads();
+  }
+}
+
+int split_thin(const GemmProb* p, int np, GemmProb* reg, GemmProb* thin,
+               int* nthin) {
+  int nr = 0;
+  *nthin = 0;
+  for (int i = 0; i < np; ++i) {
+    if (p[i].M <= 0 || p[i].N <= 0) continue;
+    if (is_thin(p[i]))
+      thin[(*nthin)++] = p[i];
+    else
+      reg[nr++] = p[i];
+  }
+  return nr;
+}
+
+int grouped_tiles(const GemmProb* p, int np, double alpha, double beta,
+                  double* scratch, cudaStream_t st);
+
 }  // namespace
 
 int64_t gemm_scratch_doubles(const GemmProb* p, int np) {
-  return make_plan(p, np).scratch;
+  GemmProb reg[GEMM_MAXPROB], thin[GEMM_MAXPROB];
+  int nt;
+  const int nr = split_thin(p, np, reg, thin, &nt);
+  int64_t s = make_plan(reg, nr).scratch;
+  for (int i = 0; i < nt; ++i)
+    s += (int64_t)thin_blocks(thin[i]) * thin[i].M * thin[i].N;
+  return s;
 }
 
 int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
                    double* scratch, cudaStream_t st) {
+  GemmProb reg[GEMM_MAXPROB], thin[GEMM_MAXPROB];
+  int nt;
+  const int nr = split_thin(p, np, reg, thin, &nt);
+  int launches = grouped_tiles(reg, nr, alpha, beta, scratch, st);
+  if (nt == 0) return launches;
+  double* tpart = scratch + make_plan(reg, nr).scratch;
+  ReduceLaunch R;
+  std::memset(&R, 0, sizeof(R));
+  R.alpha = alpha;
+  R.beta = beta;
+  R.scratch = tpart;
+  int64_t off = 0, relem = 0;
+  for (int i = 0; i < nt; ++i) {
+    const GemmProb& g = thin[i];
+    const int nb = thin_blocks(g);
+    thin_kernel<<<nb, 256, 0, st>>>(g, thin_chunk(g), tpart + off);
+    ++launches;
+    R.C[i] = g.C;
+    R.M[i] = g.M;
+    R.N[i] = g.N;
+    R.ldc[i] = g.ldc;
+    R.ks[i] = nb;
+    R.poff[i] = off;
+    R.elem0[i] = relem;
+    relem += (int64_t)g.M * g.N;
+    off += (int64_t)nb * g.M * g.N;
+  }
+  R.np = nt;
+  R.elem0[nt] = relem;
+  splitk_reduce_kernel<<<1, 256, 0, st>>>(R);
+  return launches + 1;
+}
+
+namespace {
+
+int grouped_tiles(const GemmProb* p, int np, double alpha, double beta,
+                  double* scratch, cudaStream_t st) {
+  if (np <= 0) return 0;
   const Plan pl = make_plan(p, np);
   GemmLaunch L;
   std::memset(&L, 0, sizeof(L));
@@ -299,5 +402,7 @@ int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
   }
   return launches;
 }
+
+}  // namespace
 
 }  // namespace cdcc

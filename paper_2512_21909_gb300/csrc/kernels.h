@@ -28,6 +28,35 @@ int64_t gemm_scratch_doubles(const GemmProb* p, int np);
 int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
                    double* scratch, cudaStream_t st);
 
+// K-major BF16 slices of one GEMM side: [nslice][rows][Kp] (slices.cu).
+struct SlicedOp {
+  const void* data;
+  const int* exps;   // row exponents (exact slices only)
+  int rows, Kp;
+};
+// one product for the pre-sliced tensor-core GEMMs: a = op(A) (rows M),
+// b = op(B)^T (rows N); C row-major M x N
+struct TcProb {
+  SlicedOp a, b;
+  double* C;
+  int M, N, K, ldc;
+};
+int slice_kp(int K);
+// src(row,k) = trans ? src[k*ld+row] : src[row*ld+k]; dst holds
+// nslice*rows*slice_kp(K) BF16 (16-byte aligned); exps holds rows ints
+int split_float(const double* src, int rows, int K, int64_t ld, int trans,
+                int nslice, void* dst, cudaStream_t st);
+int split_exact(const double* src, int rows, int K, int64_t ld, int trans,
+                int nslice, void* dst, int* exps, cudaStream_t st);
+int64_t sliced_workspace_bytes(const GemmProb* p, int np, int nslice,
+                               bool exact);
+int tc_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
+                   int nslice, double* scratch, unsigned int* d_err,
+                   cudaStream_t st);
+int64_t tc_sliced_scratch_doubles(const TcProb* p, int np, int nslice);
+int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
+                   int nslice, unsigned int* d_err, cudaStream_t st);
+
 // Split-precision tensor-core GEMM (tc_gemm.cu): same semantics as
 // gemm64_grouped, at most 8 products, nslice BF16 slices per operand (1-3).
 // `workspace` holds tc_workspace_bytes() bytes of BF16 slices, `scratch`

@@ -302,34 +302,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// FP64 rows -> s BF16 slices, K-major [slice][row][Kp], zero padded in K.
-// src element (row, k) = trans ? src[k*ld + row] : src[row*ld + k]
-__global__ void split_kernel(const double* __restrict__ src, int rows, int K,
-                             int64_t ld, int trans,
-                             __nv_bfloat16* __restrict__ dst, int Kp, int s,
-                             int64_t slice_stride) {
-  const int64_t total = (int64_t)rows * Kp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t row, k;
-    if (!trans) {
-      row = e / Kp;
-      k = e % Kp;
-    } else {  // walk rows fastest so that the FP64 reads are coalesced
-      k = e / rows;
-      row = e % rows;
-    }
-    double x = 0.0;
-    if (k < K) x = trans ? src[k * ld + row] : src[row * ld + k];
-    const int64_t o = row * Kp + k;
-    for (int i = 0; i < s; ++i) {
-      const __nv_bfloat16 b = __float2bfloat16_rn((float)x);
-      dst[(int64_t)i * slice_stride + o] = b;
-      x -= (double)__bfloat162float(b);
-    }
-  }
-}
-
 struct ReduceL {
   double* C[TC_MAXPROB];
   int M[TC_MAXPROB], N[TC_MAXPROB], ldc[TC_MAXPROB], ks[TC_MAXPROB];
@@ -391,13 +363,11 @@ void make_map(CUtensorMap* m, const __nv_bfloat16* base, int Kp, int rows,
 struct TcPlan {
   bool swap;                     // 128-row side = logical N
   int bn, stages;
-  int rowsA[TC_MAXPROB], rowsB[TC_MAXPROB], Kp[TC_MAXPROB];
   int tm[TC_MAXPROB], tn[TC_MAXPROB], ks[TC_MAXPROB], nkb[TC_MAXPROB];
-  int64_t ws_elems;              // BF16 slice workspace
   int64_t scratch;               // FP64 split-K partials
 };
 
-TcPlan tc_plan(const GemmProb* p, int np, int s) {
+TcPlan tc_plan(const TcProb* p, int np, int s) {
   TcPlan pl;
   std::memset(&pl, 0, sizeof(pl));
   int64_t sumM = 0, sumN = 0;
@@ -414,16 +384,12 @@ TcPlan tc_plan(const GemmProb* p, int np, int s) {
   pl.stages = std::max(1, std::min(4, TC_SMEM_BUDGET / stage));
   int64_t tiles = 0;
   for (int i = 0; i < np; ++i) {
-    const int R = pl.swap ? p[i].N : p[i].M;   // 128-row side
-    const int Cc = pl.swap ? p[i].M : p[i].N;  // BN side
-    pl.rowsA[i] = R;
-    pl.rowsB[i] = Cc;
-    pl.Kp[i] = (p[i].K + 7) / 8 * 8;
+    const int R = pl.swap ? p[i].N : p[i].M;
+    const int Cc = pl.swap ? p[i].M : p[i].N;
     pl.nkb[i] = (p[i].K + TC_BK - 1) / TC_BK;
     pl.tm[i] = (R + TC_BM - 1) / TC_BM;
     pl.tn[i] = (Cc + pl.bn - 1) / pl.bn;
     tiles += (int64_t)pl.tm[i] * pl.tn[i];
-    pl.ws_elems += (int64_t)s * (R + Cc) * pl.Kp[i];
   }
   for (int i = 0; i < np; ++i) {
     pl.ks[i] = 1;
@@ -440,65 +406,31 @@ TcPlan tc_plan(const GemmProb* p, int np, int s) {
 
 }  // namespace
 
-int64_t tc_workspace_bytes(const GemmProb* p, int np, int nslice) {
-  const TcPlan pl = tc_plan(p, np, nslice);
-  return pl.ws_elems * 2 + 256 * TC_MAXPROB * 2;
-}
-
-int64_t tc_scratch_doubles(const GemmProb* p, int np, int nslice) {
+int64_t tc_sliced_scratch_doubles(const TcProb* p, int np, int nslice) {
   return tc_plan(p, np, nslice).scratch;
 }
 
-int tc_gemm_grouped(const GemmProb* pin, int np_in, double alpha, double beta,
-                    int nslice, void* workspace, double* scratch,
-                    unsigned int* d_err, cudaStream_t st) {
-  GemmProb p[TC_MAXPROB];
-  int np = 0;
-  for (int i = 0; i < np_in; ++i)
-    if (pin[i].M > 0 && pin[i].N > 0) {
-      if (np == TC_MAXPROB) throw std::runtime_error("tc: too many blocks");
-      p[np++] = pin[i];
-    }
-  if (np == 0) return 0;
+int tc_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
+                   int nslice, double* scratch, unsigned int* d_err,
+                   cudaStream_t st) {
+  if (np <= 0) return 0;
+  if (np > TC_MAXPROB) throw std::runtime_error("tc: too many blocks");
   if (nslice < 1 || nslice > 3) throw std::runtime_error("tc: nslice");
   const TcPlan pl = tc_plan(p, np, nslice);
   TcLaunch* L = new TcLaunch;
   std::memset(L, 0, sizeof(TcLaunch));
   ReduceL R;
   std::memset(&R, 0, sizeof(R));
-  int launches = 0;
-  __nv_bfloat16* ws = (__nv_bfloat16*)workspace;
-  int64_t off = 0, poff = 0, relem = 0;
+  int64_t poff = 0, relem = 0;
   int tiles = 0, nr = 0;
   for (int i = 0; i < np; ++i) {
-    const GemmProb& g = p[i];
-    const int Kp = pl.Kp[i];
-    // logical A (M x K) and B^T (N x K), both K-major
-    __nv_bfloat16* As = ws + off;
-    off += (int64_t)nslice * g.M * Kp;
-    off = (off + 127) / 128 * 128;
-    __nv_bfloat16* Bs = ws + off;
-    off += (int64_t)nslice * g.N * Kp;
-    off = (off + 127) / 128 * 128;
-    {
-      const int64_t tot = (int64_t)g.M * Kp;
-      const int blocks = (int)std::max<int64_t>(
-          1, std::min<int64_t>((tot + 255) / 256, 152 * 16));
-      split_kernel<<<blocks, 256, 0, st>>>(g.A, g.M, g.K, g.lda, g.ta, As, Kp,
-                                           nslice, (int64_t)g.M * Kp);
-      const int64_t totb = (int64_t)g.N * Kp;
-      const int blocksb = (int)std::max<int64_t>(
-          1, std::min<int64_t>((totb + 255) / 256, 152 * 16));
-      // B^T(n, k) = op(B)(k, n): stored N x K when tb, else K x N
-      split_kernel<<<blocksb, 256, 0, st>>>(g.B, g.N, g.K, g.ldb, g.tb ? 0 : 1,
-                                            Bs, Kp, nslice,
-                                            (int64_t)g.N * Kp);
-      launches += 2;
-    }
-    const __nv_bfloat16* rowsrc = pl.swap ? Bs : As;
-    const __nv_bfloat16* colsrc = pl.swap ? As : Bs;
-    make_map(&L->ta[i], rowsrc, Kp, pl.rowsA[i], nslice, TC_BM);
-    make_map(&L->tb[i], colsrc, Kp, pl.rowsB[i], nslice, pl.bn);
+    const TcProb& g = p[i];
+    const SlicedOp& rowop = pl.swap ? g.b : g.a;
+    const SlicedOp& colop = pl.swap ? g.a : g.b;
+    make_map(&L->ta[i], (const __nv_bfloat16*)rowop.data, rowop.Kp,
+             rowop.rows, nslice, TC_BM);
+    make_map(&L->tb[i], (const __nv_bfloat16*)colop.data, colop.Kp,
+             colop.rows, nslice, pl.bn);
     L->C[i] = g.C;
     L->M[i] = g.M;
     L->N[i] = g.N;
@@ -535,16 +467,11 @@ int tc_gemm_grouped(const GemmProb* pin, int np_in, double alpha, double beta,
   L->err = d_err;
   const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
   const int smem = pl.stages * stage + 1024 + 256;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(tc_gemm_kernel,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         227 * 1024);
-    attr_set = true;
-  }
+  cudaFuncSetAttribute(tc_gemm_kernel,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   tc_gemm_kernel<<<tiles, TC_THREADS, smem, st>>>(*L);
   delete L;
-  ++launches;
+  int launches = 1;
   if (nr > 0) {
     R.np = nr;
     R.elem0[nr] = relem;
@@ -556,6 +483,108 @@ int tc_gemm_grouped(const GemmProb* pin, int np_in, double alpha, double beta,
     ++launches;
   }
   return launches;
+}
+
+// ---- convenience: slice both operands of plain GemmProbs into `workspace`
+namespace {
+int prepare_sliced(const GemmProb* pin, int np_in, int nslice, bool exact,
+                   void* workspace, TcProb* out, cudaStream_t st,
+                   int* launches) {
+  uint8_t* ws = (uint8_t*)workspace;
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    uint8_t* q = ws + off;
+    off += (bytes + 1023) / 1024 * 1024;
+    return q;
+  };
+  int np = 0;
+  for (int i = 0; i < np_in; ++i) {
+    const GemmProb& g = pin[i];
+    if (g.M <= 0 || g.N <= 0) continue;
+    const int Kp = slice_kp(g.K);
+    TcProb t;
+    std::memset(&t, 0, sizeof(t));
+    t.C = g.C;
+    t.M = g.M;
+    t.N = g.N;
+    t.K = g.K;
+    t.ldc = g.ldc;
+    void* da = take((int64_t)nslice * g.M * Kp * 2);
+    void* db = take((int64_t)nslice * g.N * Kp * 2);
+    int* ea = exact ? (int*)take((int64_t)g.M * 4) : nullptr;
+    int* eb = exact ? (int*)take((int64_t)g.N * 4) : nullptr;
+    // op(A)(m,k): A[m][k] (ta = 0) or A[k][m];  op(B)^T(n,k): B[n][k] (tb)
+    // or B[k][n]
+    if (exact) {
+      *launches += split_exact(g.A, g.M, g.K, g.lda, g.ta, nslice, da, ea, st);
+      *launches += split_exact(g.B, g.N, g.K, g.ldb, g.tb ? 0 : 1, nslice, db,
+                               eb, st);
+    } else {
+      *launches += split_float(g.A, g.M, g.K, g.lda, g.ta, nslice, da, st);
+      *launches += split_float(g.B, g.N, g.K, g.ldb, g.tb ? 0 : 1, nslice, db,
+                               st);
+    }
+    t.a = {da, ea, g.M, Kp};
+    t.b = {db, eb, g.N, Kp};
+    out[np++] = t;
+  }
+  return np;
+}
+}  // namespace
+
+int64_t sliced_workspace_bytes(const GemmProb* p, int np, int nslice,
+                               bool exact) {
+  int64_t b = 0;
+  for (int i = 0; i < np; ++i) {
+    if (p[i].M <= 0 || p[i].N <= 0) continue;
+    const int64_t Kp = slice_kp(p[i].K);
+    b += (int64_t)nslice * (p[i].M + p[i].N) * Kp * 2 + 4 * 1024;
+    if (exact) b += (int64_t)(p[i].M + p[i].N) * 4;
+  }
+  return b + 1024;
+}
+
+int64_t tc_workspace_bytes(const GemmProb* p, int np, int nslice) {
+  return sliced_workspace_bytes(p, np, nslice, false);
+}
+
+int64_t tc_scratch_doubles(const GemmProb* p, int np, int nslice) {
+  TcProb t[TC_MAXPROB];
+  int n = 0;
+  for (int i = 0; i < np && n < TC_MAXPROB; ++i)
+    if (p[i].M > 0 && p[i].N > 0) {
+      std::memset(&t[n], 0, sizeof(TcProb));
+      t[n].M = p[i].M;
+      t[n].N = p[i].N;
+      t[n].K = p[i].K;
+      ++n;
+    }
+  return tc_plan(t, n, nslice).scratch;
+}
+
+int tc_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
+                    int nslice, void* workspace, double* scratch,
+                    unsigned int* d_err, cudaStream_t st) {
+  TcProb t[TC_MAXPROB];
+  int launches = 0;
+  const int n = prepare_sliced(p, np, nslice, false, workspace, t, st,
+                               &launches);
+  return launches + tc_gemm_sliced(t, n, alpha, beta, nslice, scratch, d_err,
+                                   st);
+}
+
+int64_t oz_workspace_bytes(const GemmProb* p, int np, int nslice) {
+  return sliced_workspace_bytes(p, np, nslice, true);
+}
+
+int oz_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
+                    int nslice, void* workspace, unsigned int* d_err,
+                    cudaStream_t st) {
+  TcProb t[TC_MAXPROB];
+  int launches = 0;
+  const int n = prepare_sliced(p, np, nslice, true, workspace, t, st,
+                               &launches);
+  return launches + oz_gemm_sliced(t, n, alpha, beta, nslice, d_err, st);
 }
 
 }  // namespace cdcc

@@ -336,56 +336,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   }
 }
 
-// exponent e of every row: max_k |x(row,k)| < 2^e (0 for an all-zero row)
-__global__ void oz_rowexp_kernel(const double* __restrict__ src, int rows,
-                                 int K, int64_t ld, int trans,
-                                 int* __restrict__ e) {
-  if (!trans) {  // one warp per row, coalesced along k
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= rows) return;
-    double m = 0.0;
-    for (int k = lane; k < K; k += 32) m = fmax(m, fabs(src[(int64_t)w * ld + k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) e[w] = (m > 0.0) ? ilogb(m) + 1 : 0;
-  } else {       // one thread per row, coalesced across rows
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    double m = 0.0;
-    for (int k = 0; k < K; ++k) m = fmax(m, fabs(src[(int64_t)k * ld + r]));
-    e[r] = (m > 0.0) ? ilogb(m) + 1 : 0;
-  }
-}
-
-// integer slices (see file header), K-major [slice][row][Kp]
-__global__ void oz_split_kernel(const double* __restrict__ src, int rows,
-                                int K, int64_t ld, int trans,
-                                const int* __restrict__ e,
-                                __nv_bfloat16* __restrict__ dst, int Kp, int s,
-                                int64_t slice_stride) {
-  const int64_t total = (int64_t)rows * Kp;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t row, k;
-    if (!trans) {
-      row = idx / Kp;
-      k = idx % Kp;
-    } else {
-      k = idx / rows;
-      row = idx % rows;
-    }
-    double x = 0.0;
-    if (k < K) x = trans ? src[k * ld + row] : src[row * ld + k];
-    double y = ldexp(x, 8 - e[row]);            // |y| < 256
-    const int64_t o = row * Kp + k;
-    for (int i = 0; i < s; ++i) {
-      const double q = rint(y);
-      dst[(int64_t)i * slice_stride + o] = __float2bfloat16_rn((float)q);
-      y = (y - q) * 128.0;                      // |y| <= 64
-    }
-  }
-}
-
 PFN_cuTensorMapEncodeTiled_v12000 oz_encode = nullptr;
 std::once_flag oz_once;
 
@@ -418,7 +368,7 @@ void oz_map(CUtensorMap* m, const __nv_bfloat16* base, int Kp, int rows, int s,
                              std::to_string((int)r));
 }
 
-bool oz_swap(const GemmProb* p, int np) {
+bool oz_swap(const TcProb* p, int np) {
   int64_t sm = 0, sn = 0;
   for (int i = 0; i < np; ++i) {
     sm += p[i].M;
@@ -429,85 +379,32 @@ bool oz_swap(const GemmProb* p, int np) {
 
 }  // namespace
 
-int64_t oz_workspace_bytes(const GemmProb* p, int np, int nslice) {
-  int64_t b = 0;
-  for (int i = 0; i < np; ++i) {
-    if (p[i].M <= 0 || p[i].N <= 0) continue;
-    const int64_t Kp = (p[i].K + 7) / 8 * 8;
-    // four regions per block, each rounded up to 1 KiB
-    b += (int64_t)nslice * (p[i].M + p[i].N) * Kp * 2;
-    b += (int64_t)(p[i].M + p[i].N) * 4 + 4 * 1024;
-  }
-  return b + 1024;
-}
-
-int oz_gemm_grouped(const GemmProb* pin, int np_in, double alpha, double beta,
-                    int nslice, void* workspace, unsigned int* d_err,
-                    cudaStream_t st) {
-  GemmProb p[OZ_MAXPROB];
-  int np = 0;
-  for (int i = 0; i < np_in; ++i)
-    if (pin[i].M > 0 && pin[i].N > 0) {
-      if (np == OZ_MAXPROB) throw std::runtime_error("oz: too many blocks");
-      p[np++] = pin[i];
-    }
-  if (np == 0) return 0;
+int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
+                   int nslice, unsigned int* d_err, cudaStream_t st) {
+  if (np <= 0) return 0;
+  if (np > OZ_MAXPROB) throw std::runtime_error("oz: too many blocks");
   if (nslice < 2 || nslice > OZ_MAXS) throw std::runtime_error("oz: nslice");
   const bool swap = oz_swap(p, np);
   OzLaunch* L = new OzLaunch;
   std::memset(L, 0, sizeof(OzLaunch));
-  uint8_t* ws = (uint8_t*)workspace;
-  int64_t off = 0;
-  auto take = [&](int64_t bytes) {
-    uint8_t* q = ws + off;
-    off += (bytes + 1023) / 1024 * 1024;
-    return q;
-  };
-  int launches = 0, tiles = 0;
+  int tiles = 0;
   for (int i = 0; i < np; ++i) {
-    const GemmProb& g = p[i];
-    const int Kp = (g.K + 7) / 8 * 8;
-    __nv_bfloat16* As = (__nv_bfloat16*)take((int64_t)nslice * g.M * Kp * 2);
-    __nv_bfloat16* Bs = (__nv_bfloat16*)take((int64_t)nslice * g.N * Kp * 2);
-    int* ea = (int*)take((int64_t)g.M * 4);
-    int* eb = (int*)take((int64_t)g.N * 4);
-    // op(A) rows: A[m][k] (ta = 0) or A stored [k][m];  B^T rows: B stored
-    // [n][k] (tb) or [k][n]
-    const int btr = g.tb ? 0 : 1;
-    if (!g.ta)
-      oz_rowexp_kernel<<<(g.M * 32 + 255) / 256, 256, 0, st>>>(g.A, g.M, g.K,
-                                                               g.lda, 0, ea);
-    else
-      oz_rowexp_kernel<<<(g.M + 255) / 256, 256, 0, st>>>(g.A, g.M, g.K,
-                                                          g.lda, 1, ea);
-    if (!btr)
-      oz_rowexp_kernel<<<(g.N * 32 + 255) / 256, 256, 0, st>>>(g.B, g.N, g.K,
-                                                               g.ldb, 0, eb);
-    else
-      oz_rowexp_kernel<<<(g.N + 255) / 256, 256, 0, st>>>(g.B, g.N, g.K,
-                                                          g.ldb, 1, eb);
-    const int64_t ta_ = (int64_t)g.M * Kp, tb_ = (int64_t)g.N * Kp;
-    const int bla = (int)std::max<int64_t>(
-        1, std::min<int64_t>((ta_ + 255) / 256, 152 * 16));
-    const int blb = (int)std::max<int64_t>(
-        1, std::min<int64_t>((tb_ + 255) / 256, 152 * 16));
-    oz_split_kernel<<<bla, 256, 0, st>>>(g.A, g.M, g.K, g.lda, g.ta, ea, As,
-                                         Kp, nslice, ta_);
-    oz_split_kernel<<<blb, 256, 0, st>>>(g.B, g.N, g.K, g.ldb, btr, eb, Bs,
-                                         Kp, nslice, tb_);
-    launches += 4;
-    const int R = swap ? g.N : g.M, Cc = swap ? g.M : g.N;
-    oz_map(&L->ta[i], swap ? Bs : As, Kp, R, nslice, OZ_BM);
-    oz_map(&L->tb[i], swap ? As : Bs, Kp, Cc, nslice, OZ_BN);
-    L->erow[i] = swap ? eb : ea;
-    L->ecol[i] = swap ? ea : eb;
+    const TcProb& g = p[i];
+    const SlicedOp& rowop = swap ? g.b : g.a;
+    const SlicedOp& colop = swap ? g.a : g.b;
+    oz_map(&L->ta[i], (const __nv_bfloat16*)rowop.data, rowop.Kp, rowop.rows,
+           nslice, OZ_BM);
+    oz_map(&L->tb[i], (const __nv_bfloat16*)colop.data, colop.Kp, colop.rows,
+           nslice, OZ_BN);
+    L->erow[i] = rowop.exps;
+    L->ecol[i] = colop.exps;
     L->C[i] = g.C;
     L->M[i] = g.M;
     L->N[i] = g.N;
     L->ldc[i] = g.ldc;
     L->nkb[i] = (g.K + OZ_BK - 1) / OZ_BK;
-    L->tm[i] = (R + OZ_BM - 1) / OZ_BM;
-    L->tn[i] = (Cc + OZ_BN - 1) / OZ_BN;
+    L->tm[i] = (rowop.rows + OZ_BM - 1) / OZ_BM;
+    L->tn[i] = (colop.rows + OZ_BN - 1) / OZ_BN;
     L->tile0[i] = tiles;
     tiles += L->tm[i] * L->tn[i];
   }
@@ -524,7 +421,7 @@ int oz_gemm_grouped(const GemmProb* pin, int np_in, double alpha, double beta,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   oz_gemm_kernel<<<tiles, OZ_THREADS, smem, st>>>(*L);
   delete L;
-  return launches + 1;
+  return 1;
 }
 
 }  // namespace cdcc

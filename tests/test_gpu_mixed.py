@@ -36,7 +36,8 @@ def cd():
 
 
 SHAPES = [(1, 1, 1), (5, 3, 7), (128, 128, 64), (200, 37, 300),
-          (32, 700, 650), (300, 290, 5000), (129, 257, 77), (64, 32, 1000)]
+          (32, 700, 650), (300, 290, 5000), (129, 257, 77), (64, 32, 1000),
+          (1, 1, 5000), (7, 9, 9000)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
