@@ -13,6 +13,8 @@ Modules
   fci2        exact two-electron singlet FCI (pin for o = 1)
   brute       determinant-space projection <mu|exp(-T) H exp(T)|0> (pin)
   mp2         closed-form MP2 energy (pin for the first iteration)
+  rows        energy and residual rows at given amplitudes, no full ladder
+              (checks at sizes where the full residual is too slow)
 
 Parity status of each function is stated in its docstring; every function
 used by the GPU parity tests is pinned by a `-m "not gpu"` test.

@@ -156,7 +156,7 @@ def _draw_symmetric_pattern(rng, nirrep, norb, chol, amp_of, gx=0):
         for gp in range(nirrep):
             gq = gp ^ gP ^ gx
             blk = 0.5 * (X[gp] + X[gq].transpose(0, 2, 1))
-            out.append((amp * blk).reshape(nP, -1))
+            out.append((amp * blk).reshape(nP, norb[gp] * norb[gq]))
     # reorder to G_P, k, G_p: the blocks above are grouped per G_P as
     # [G_p=0 (nP x ...), G_p=1 ...]; interleave per vector k
     flat = []

@@ -17,7 +17,7 @@ import torch
 from synth import (random_system, unpack_dense, pack_dense, make_system,
                    make_displacements, make_displacement_nontotsym,
                    irrep_split, chol_split)
-from oracle import brute, ccsd, model, lagrangian, fci2, mp2
+from oracle import brute, ccsd, model, lagrangian, fci2, mp2, rows
 
 DT = torch.float64
 
@@ -269,3 +269,46 @@ def test_euler_identity():
     assert abs(lhs - rhs) < 1e-11
     # the 1-RDM traces to the electron count
     assert abs(np.trace(r["D"].numpy()) - 2 * s.nocc) < 1e-11
+
+
+@pytest.mark.parametrize("occ,vir,chol,seed", CASES)
+def test_rows_and_energy_equal_determinant_projection(occ, vir, chol, seed):
+    """oracle.rows (residual rows and energy without the full ladder) against
+    the brute-force projections, on unsymmetrised t2 and non-canonical h."""
+    s = random_system(list(occ), list(vir), list(chol), seed=seed, scale=0.8)
+    L = unpack_dense(s, s.L)
+    rng = np.random.default_rng(seed + 50)
+    n, o, v = s.n, s.nocc, s.nvir
+    h = rng.standard_normal((n, n)) * 0.3
+    h = 0.5 * (h + h.T)
+    t1 = rng.standard_normal((o, v)) * 0.15
+    t2 = rng.standard_normal((o, o, v, v)) * 0.15
+    Eb, R1b, R2b = brute.projections(h, L, o, t1,
+                                     0.5 * (t2 + t2.transpose(1, 0, 3, 2)))
+    assert abs(rows.energy(T(t1), T(t2), T(h), T(L), o) - Eb) < 1e-12
+    pairs = [(i, j) for i in range(o) for j in range(o)]
+    R1, R2 = rows.residual_rows(T(t1), T(t2), T(h), T(L), o, pairs)
+    assert np.abs(R1.numpy() - R1b).max() < 1e-12
+    for p in pairs:
+        assert np.abs(R2[p].numpy() - R2b[p]).max() < 1e-12
+
+
+def test_rows_planted_mistake_is_caught(monkeypatch):
+    """Dropping the ladder from the row evaluation breaks the projection pin."""
+    s = random_system([2], [3], [5], seed=11, scale=0.8)
+    L = unpack_dense(s, s.L)
+    rng = np.random.default_rng(11)
+    h = np.diag(s.eps)
+    t1, t2 = _random_amps(rng, 2, 3, 0.2)
+    _, _, R2b = brute.projections(h, L, 2, t1, t2)
+    real = torch.matmul
+    calls = {"n": 0}
+
+    def no_ladder(a, b):                       # zero the PPL product
+        calls["n"] += 1
+        r = real(a, b)
+        return r * 0.0 if a.dim() == 3 else r
+    monkeypatch.setattr(rows.torch, "matmul", no_ladder)
+    _, R2 = rows.residual_rows(T(t1), T(t2), T(h), T(L), 2, [(0, 1)])
+    assert calls["n"] > 0
+    assert np.abs(R2[(0, 1)].numpy() - R2b[0, 1]).max() > 1e-4
