@@ -45,35 +45,26 @@ def parse():
                     choices=["fp64", "mixed", "tc"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--others", default="all",
+                    help="other schedules to time beside --precision: "
+                         "'all', 'none' or a comma list")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     return ap.parse_args()
 
 
 def dist_init():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    if ws > 1:
-        import torch.distributed as dist
-        backend = "nccl" if os.environ.get("CDCC_BENCH_GLOO") is None \
-            else "gloo"
-        dist.init_process_group(backend)
-    return rank, ws
+    from paper_2512_21909_gb300 import replicas
+    return replicas.init()
 
 
 def barrier(ws):
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2512_21909_gb300 import replicas
+    replicas.barrier(ws)
 
 
 def allmax(x, ws):
-    if ws == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64,
-                     device="cuda" if torch.cuda.is_available() else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2512_21909_gb300 import replicas
+    return replicas.allmax(x, ws)
 
 
 # ---------------------------------------------------------------- clocks
@@ -271,7 +262,9 @@ def run_ours(args, rank, ws):
     # ---- the other schedules on the same workload (mixed / TC vs FP64 GPU)
     saved = args.precision
     other_lines = []
-    for other in [p for p in ("fp64", "mixed", "tc") if p != saved]:
+    wanted = ("fp64", "mixed", "tc") if args.others == "all" else \
+        tuple(x for x in args.others.split(",") if x and x != "none")
+    for other in [p for p in wanted if p != saved]:
         args.precision = other
         one(L_d, dL_d)                   # warm-up of the other schedule
         o_times = []
@@ -296,13 +289,13 @@ def run_ours(args, rank, ws):
 
     # ---- end to end through the C ABI with host buffers
     e2e = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(0, min(args.steps, args.e2e_steps))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         one(L_h.numpy(), dL_h.numpy())
         e2e.append(time.perf_counter() - t0)
-    e2e50 = allmax(float(np.median(e2e)), ws)
+    e2e50 = allmax(float(np.median(e2e)), ws) if e2e else None
     h2d = (s.L.nbytes + dL.nbytes + s.eps.nbytes + s.orb_irrep.nbytes
            + s.chol_irrep.nbytes)
     d2h = 8 * (nx + 1)
@@ -364,9 +357,8 @@ def main():
         run_reference(args, rank, ws)
     else:
         run_ours(args, rank, ws)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    from paper_2512_21909_gb300 import replicas
+    replicas.finalize(ws)
 
 
 if __name__ == "__main__":

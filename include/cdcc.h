@@ -68,6 +68,18 @@ typedef enum {
                              large contraction on the tensor cores         */
 } cdcc_precision;
 
+/* How the particle-particle ladder gets its (ac|bd) integrals.           */
+typedef enum {
+    CDCC_LADDER_AUTO = 0,   /* STORED when its estimated footprint is below
+                               40 % of the free device memory at init,
+                               else OTF                                    */
+    CDCC_LADDER_STORED = 1, /* (ac|bd) of the undressed vectors built once
+                               per gradient and kept in device memory      */
+    CDCC_LADDER_OTF = 2     /* assembled from L^P_ab in row batches every
+                               time the ladder is applied (Sec. 2.3); only
+                               two batches are resident                    */
+} cdcc_ladder;
+
 typedef void *(*cdcc_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*cdcc_free_fn)(void *ptr, size_t bytes, void *stream,
                              void *user);
@@ -85,6 +97,8 @@ typedef struct {
     cdcc_alloc_fn dev_alloc;/* optional device allocator                    */
     cdcc_free_fn dev_free;
     void *alloc_user;
+    int ladder;             /* cdcc_ladder (default CDCC_LADDER_AUTO)       */
+    double ladder_batch_gb; /* OTF: GB of one (ab|cd) row batch (default 2) */
 } cdcc_options;
 
 typedef struct cdcc_ctx cdcc_ctx;
@@ -215,6 +229,9 @@ cdcc_status cdcc_kernel_stats(cdcc_ctx *ctx, int kind, double *seconds,
  * CCSD FP64, Lambda mixed-precision, Lambda FP64 iterations. */
 cdcc_status cdcc_solver_info(cdcc_ctx *ctx, int *info);
 
+/* The ladder mode the context chose (CDCC_LADDER_STORED or _OTF).         */
+cdcc_status cdcc_ladder_mode(cdcc_ctx *ctx, int *mode);
+
 /*
  * C = beta*C + alpha * op(A) op(B) on device buffers, row-major, with the
  * library's contraction kernels (the building block of every contraction of
@@ -235,6 +252,16 @@ cdcc_status cdcc_dgemm(int transA, int transB, int M, int N, int K,
                        double alpha, const double *A, int lda,
                        const double *B, int ldb, double beta, double *C,
                        int ldc, int mode, void *stream);
+
+/*
+ * Self-test of the failure path of bounded device waits (no paper
+ * counterpart): launches one kernel whose mbarrier wait can never complete;
+ * the bounded spin gives up, the kernel records an error code and exits.
+ * Returns CDCC_ETIMEOUT when that path works (the expected result), CDCC_OK
+ * if the wait unexpectedly completed, CDCC_ECUDA / CDCC_ENOMEM on a runtime
+ * error.  The device stays usable afterwards.
+ */
+cdcc_status cdcc_selftest_bounded_wait(void *stream);
 
 /* Number of kernels this context has launched so far. */
 long long cdcc_kernel_launches(const cdcc_ctx *ctx);

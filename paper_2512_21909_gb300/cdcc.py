@@ -23,6 +23,7 @@ STATUS = {0: "CDCC_OK", 1: "CDCC_EINVAL", 2: "CDCC_ENOMEM", 3: "CDCC_ENOCONV",
           4: "CDCC_ENUMERIC", 5: "CDCC_ECUDA", 6: "CDCC_ESTATE",
           7: "CDCC_ETIMEOUT"}
 PREC_FP64, PREC_MIXED, PREC_TC = 0, 1, 2
+LADDER_AUTO, LADDER_STORED, LADDER_OTF = 0, 1, 2
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                             ctypes.c_void_p)
@@ -36,7 +37,8 @@ class cdcc_options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("switch_tol", ctypes.c_double),
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", ctypes.c_void_p)]
+                ("alloc_user", ctypes.c_void_p), ("ladder", ctypes.c_int),
+                ("ladder_batch_gb", ctypes.c_double)]
 
 
 class CdccError(RuntimeError):
@@ -305,6 +307,16 @@ def cdcc_solver_info(ctx):
     return tuple(int(x) for x in info)
 
 
+def cdcc_ladder_mode(ctx) -> int:
+    """LADDER_STORED or LADDER_OTF, as chosen by the context."""
+    lib = load()
+    lib.cdcc_ladder_mode.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.cdcc_ladder_mode.restype = ctypes.c_int
+    m = ctypes.c_int(0)
+    _check(ctx, lib.cdcc_ladder_mode(ctx.handle, ctypes.byref(m)))
+    return m.value
+
+
 def cdcc_dgemm(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc,
                mode=0, stream=None):
     """C = beta C + alpha op(A) op(B) on CUDA tensors (row-major)."""
@@ -372,6 +384,18 @@ def cdcc_contract_dL_noalloc(gamma, dL, nx, nnz, g, stream=None):
         ctypes.c_void_p(int(stream)))
     if st != CDCC_OK:
         raise CdccError(st, "cdcc_contract_dL_noalloc failed")
+
+
+def cdcc_selftest_bounded_wait(stream=None) -> int:
+    """Run the bounded-wait self-test; returns the cdcc_status code
+    (CDCC_ETIMEOUT means the give-up path works)."""
+    lib = load()
+    lib.cdcc_selftest_bounded_wait.argtypes = [ctypes.c_void_p]
+    lib.cdcc_selftest_bounded_wait.restype = ctypes.c_int
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    return int(lib.cdcc_selftest_bounded_wait(ctypes.c_void_p(int(stream))))
 
 
 def init_from_system(sysm, **kw) -> Context:

@@ -136,6 +136,7 @@ struct cdcc_ctx {
   Diis cc_diis, lam_diis;
   unsigned int* d_err = nullptr;
   int iters_mixed[2] = {0, 0}, iters_fp64[2] = {0, 0};
+  bool otf = false;   // ladder assembled on the fly (no stored W0)
 };
 
 namespace {
@@ -191,11 +192,14 @@ void prepare(cdcc_ctx* c) {
   e.contract(1.0, c->Lov, "Pia", c->Lov, "Pjb", 0.0, c->Govov, "iajb");
   c->Govvv = e.tensor("Govvv", {SO, SV, SV, SV}, 2);
   e.contract(1.0, c->Lov, "Pmc", c->Lvv, "Pbd", 0.0, c->Govvv, "mcbd");
+  c->Govov->symmetric = true;   // (ia|jb) is a symmetric matrix per block
+  c->Govov->constant = c->Govvv->constant = true;
+  if (c->otf) return;           // the ladder builds its integrals itself
   c->W0 = e.tensor("W0", {SV, SV, SV, SV}, 2);
   e.contract(1.0, c->Lvv, "Pac", c->Lvv, "Pbd", 0.0, c->W0, "abcd");
-  // (ia|jb) and W0[(ab),(cd)] = (ac|bd) are symmetric matrices per block
-  c->Govov->symmetric = c->W0->symmetric = true;
-  c->Govov->constant = c->Govvv->constant = c->W0->constant = true;
+  // W0[(ab),(cd)] = (ac|bd) is a symmetric matrix per block
+  c->W0->symmetric = true;
+  c->W0->constant = true;
 }
 
 // ------------------------------------------------------------------ residual
@@ -290,7 +294,10 @@ void residual(cdcc_ctx* c) {
   // Lhat_vv = L_vv - t1^T L_ov, expanded so that only the undressed W0 (built
   // once per gradient) enters the O(o^2 v^4) product:
   //   (ac|bd)^ = (ac|bd) - t_m^a (mc|bd) - t_n^b (ac|nd) + t_m^a t_n^b (mc|nd)
-  e.contract(1.0, t2s, "ijcd", c->W0, "abcd", 1.0, Rr, "ijab");  // PPL
+  if (c->otf)
+    e.ladder(1.0, t2s, c->Lvv, Rr);                              // PPL
+  else
+    e.contract(1.0, t2s, "ijcd", c->W0, "abcd", 1.0, Rr, "ijab"); // PPL
   Tensor* Yl = T("Ylad", {SO, SO, SO, SV}, 2);
   e.contract(1.0, t2s, "ijcd", c->Govvv, "mcbd", 0.0, Yl, "ijmb");
   e.contract(-1.0, T1, "ma", Yl, "ijmb", 1.0, Rr, "ijab");
@@ -871,6 +878,27 @@ void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
     e.contract(1.0, c->Lvo, "Pak", c->Lov, "Pkb", 1.0, c->hvv, "ab");
   }
   c->hoo->tag = c->hov->tag = c->hvo->tag = c->hvv->tag = TAG_H;
+  // ladder mode: the stored (ab|cd) integrals cost 8 bytes per element, the
+  // density sweep adds their adjoint, and the tensor-core schedules cache
+  // slices of both (factors below); on the fly only two row batches live
+  {
+    const Layout lw = e.layout({SV, SV, SV, SV}, 2);
+    const double k = c->opt.precision == CDCC_PREC_TC      ? 4.5
+                     : c->opt.precision == CDCC_PREC_MIXED ? 3.5
+                                                           : 2.0;
+    const double stored = 8.0 * (double)lw.size * k;
+    size_t fre = 0, tot = 0;
+    CK(cudaMemGetInfo(&fre, &tot));
+    if (c->opt.ladder == CDCC_LADDER_STORED)
+      c->otf = false;
+    else if (c->opt.ladder == CDCC_LADDER_OTF)
+      c->otf = true;
+    else
+      c->otf = stored > 0.4 * (double)fre;
+    const double gb = c->opt.ladder_batch_gb > 0 ? c->opt.ladder_batch_gb
+                                                 : 2.0;
+    e.ladder_batch_bytes = (int64_t)(gb * 1e9);
+  }
   {
     std::vector<double> h = to_host(c, c->hoo);
     double tr = 0;
@@ -978,6 +1006,8 @@ void cdcc_default_options(cdcc_options* o) {
   o->switch_tol = 1e-6;
   o->device = 0;
   o->stream = nullptr;
+  o->ladder = CDCC_LADDER_AUTO;
+  o->ladder_batch_gb = 2.0;
 }
 
 cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
@@ -994,6 +1024,9 @@ cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
     cdcc_default_options(&c->opt);
   if (c->opt.max_iter <= 0) c->opt.max_iter = 100;
   cdcc_status s = guarded(c, [&] {
+    if (c->opt.precision < CDCC_PREC_FP64 || c->opt.precision > CDCC_PREC_TC ||
+        c->opt.ladder < CDCC_LADDER_AUTO || c->opt.ladder > CDCC_LADDER_OTF)
+      throw StatusError(CDCC_EINVAL, "unknown precision or ladder mode");
     init_ctx(c, nirrep, nocc, nvir, nchol, orb_irrep, eps, chol_irrep, L);
   });
   *out = c;  // also on error, so that cdcc_last_error can be read
@@ -1105,6 +1138,12 @@ cdcc_status cdcc_kernel_stats(cdcc_ctx* c, int kind, double* seconds,
     if (launches) *launches = (long long)c->eng->prof_n[kind];
     if (work) *work = c->eng->prof_work[kind];
   });
+}
+
+cdcc_status cdcc_ladder_mode(cdcc_ctx* c, int* mode) {
+  if (!c || !mode) return CDCC_EINVAL;
+  *mode = c->otf ? CDCC_LADDER_OTF : CDCC_LADDER_STORED;
+  return CDCC_OK;
 }
 
 cdcc_status cdcc_solver_info(cdcc_ctx* c, int* info) {

@@ -57,6 +57,8 @@ Engine::~Engine() {
     al.release(kv.second.chunks, kv.second.nchunk * sizeof(Chunk));
   }
   for (auto& b : pool_) al.release(b.d, (size_t)b.n * 8);
+  if (lad_x_) al.release(lad_x_, (size_t)lad_n_ * 8);
+  if (lad_w_) al.release(lad_w_, (size_t)lad_n_ * 8);
   for (auto& kv : slice_cache_) {
     al.release(kv.second.data, kv.second.bytes);
     if (kv.second.exps) al.release(kv.second.exps, kv.second.ebytes);
@@ -558,33 +560,12 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
     g.M = (int)M;
     g.N = (int)N;
     g.K = (int)K;
-    flops += 2 * M * N * K;
     probs[np++] = g;
   }
   double fl = 0;
   for (int i = 0; i < np; ++i)
     fl += 2.0 * probs[i].M * (double)probs[i].N * probs[i].K;
-  // tensor cores only for matrix-shaped blocks: thin products (dots, outer
-  // products, o x o results) stay on the FP64 path with split K
-  double fl_tc = 0;
-  for (int i = 0; i < np; ++i) {
-    const GemmProb& g = probs[i];
-    if (std::min(g.M, g.N) >= 32 && std::max(g.M, g.N) >= 128 && g.K >= 128)
-      fl_tc += 2.0 * g.M * (double)g.N * g.K;
-  }
-  const char* path;
-  if (tc_slices_ > 0 && fl >= (double)tc_min_flops && fl_tc >= 0.9 * fl &&
-      np <= 8 && d_err) {
-    path = tc_slices_ >= 12 ? "exact" : "split";
-    tc_contract(probs, np, mp, mq, alpha, direct ? beta : 0.0, fl);
-  } else {
-    path = "fp64";
-    const int64_t sk = gemm_scratch_doubles(probs, np);
-    double* skb = sk > 0 ? scratch(sk) : nullptr;
-    timed(K_GEMM64, fl, [&] {
-      return gemm64_grouped(probs, np, alpha, direct ? beta : 0.0, skb, st_);
-    });
-  }
+  const char* path = run_gemms(probs, np, mp, mq, alpha, direct ? beta : 0.0);
   if (!direct)
     axpy_raw(1.0, *DL, Dd, best.X + best.Y, beta, C->lay, C->d, ic);
   if (tr_a) {
@@ -596,6 +577,50 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   }
   release_scratch();
   tmp_layouts_.clear();
+}
+
+// Route the blocks of one product (they write disjoint parts of C) to the
+// tensor cores or the FP64 kernel and launch them.  Tensor cores only take
+// matrix-shaped blocks: thin products (dots, outer products, o x o results)
+// stay on the FP64 path with split K.  Returns the path taken.
+const char* Engine::run_gemms(const GemmProb* probs, int np, const Mat& mp,
+                              const Mat& mq, double alpha, double beta) {
+  double fl = 0;
+  for (int i = 0; i < np; ++i) {
+    fl += 2.0 * probs[i].M * (double)probs[i].N * probs[i].K;
+    flops += 2 * (int64_t)probs[i].M * probs[i].N * probs[i].K;
+  }
+  GemmProb ptc[GEMM_MAXPROB], p64[GEMM_MAXPROB];
+  int ntc = 0, n64 = 0;
+  double fl_tc = 0;
+  for (int i = 0; i < np; ++i) {
+    const GemmProb& g = probs[i];
+    if (tc_slices_ > 0 && std::min(g.M, g.N) >= 32 &&
+        std::max(g.M, g.N) >= 64 && g.K >= 128) {
+      fl_tc += 2.0 * g.M * (double)g.N * g.K;
+      ptc[ntc++] = g;
+    } else {
+      p64[n64++] = g;
+    }
+  }
+  if (!(fl_tc >= (double)tc_min_flops && d_err)) {
+    for (int i = 0; i < ntc; ++i) p64[n64++] = ptc[i];
+    ntc = 0;
+    fl_tc = 0;
+  }
+  const char* path = ntc == 0 ? "fp64" : n64 == 0
+                         ? (tc_slices_ >= 12 ? "exact" : "split")
+                         : (tc_slices_ >= 12 ? "exact+fp64" : "split+fp64");
+  if (ntc > 0) tc_contract(ptc, ntc, mp, mq, alpha, beta, fl_tc);
+  if (n64 > 0) {
+    const double f64 = fl - fl_tc;
+    const int64_t sk = gemm_scratch_doubles(p64, n64);
+    double* skb = sk > 0 ? scratch(sk) : nullptr;
+    timed(K_GEMM64, f64, [&] {
+      return gemm64_grouped(p64, n64, alpha, beta, skb, st_);
+    });
+  }
+  return path;
 }
 
 void Engine::write_trace(const char* file) {
@@ -720,7 +745,7 @@ void Engine::backward(const std::vector<std::pair<Tensor*, Tensor*>>& seeds,
     if (t->tag & active) t->req = true;
   }
   for (const Op& op : tape_) {
-    if (op.A->req || (op.kind == 0 && op.B->req)) op.C->req = true;
+    if (op.A->req || (op.kind != 1 && op.B->req)) op.C->req = true;
   }
   // zero adjoints of everything that carries one
   std::vector<Tensor*> req;
@@ -750,6 +775,10 @@ void Engine::backward(const std::vector<std::pair<Tensor*, Tensor*>>& seeds,
       if (op.B->req)
         contract(op.alpha, op.A, op.ia.c_str(), Cb, op.ic.c_str(), 1.0,
                  adjoint(op.B), op.ib.c_str());
+    } else if (op.kind == 2) {
+      ladder_adjoint(op.alpha, Cb, op.A, op.B,
+                     op.A->req ? adjoint(op.A) : nullptr,
+                     op.B->req ? adjoint(op.B) : nullptr);
     } else {
       if (op.A->req)
         axpy(op.alpha, Cb, op.ic.c_str(), 1.0, adjoint(op.A), op.ia.c_str());

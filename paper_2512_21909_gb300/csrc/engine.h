@@ -95,6 +95,18 @@ class Engine {
   void axpy(double alpha, Tensor* X, const char* ix, double beta, Tensor* Y,
             const char* iy);
 
+  // Particle-particle ladder with the integrals assembled on the fly from
+  // the Cholesky vectors (Sec. 2.3):
+  //   R[ij,ab] += alpha * sum_cd T[ij,cd] (ac|bd),  (ac|bd) = sum_P L_ac L_bd
+  // T, R: {SO,SO,SV,SV} split 2; L: {SQ,SV,SV} split 1, every L^P symmetric.
+  // The (ab|cd) matrix is never stored whole: row batches (a in a range of
+  // one irrep, all b) are built by one grouped GEMM over P, permuted into
+  // (ab|cd) order and applied at once.  Recorded as one tape operation whose
+  // adjoint rebuilds the batches (T and L adjoints).
+  void ladder(double alpha, Tensor* T, Tensor* L, Tensor* R);
+  // device bytes of one row batch of the (ab|cd) matrix (two such buffers)
+  int64_t ladder_batch_bytes = (int64_t)2 << 30;
+
   // tape
   void record(bool on) { recording_ = on; }
   // append to the tape without executing (results already in place)
@@ -155,7 +167,7 @@ class Engine {
 
  private:
   struct Op {
-    int kind;  // 0 contract, 1 axpy
+    int kind;  // 0 contract, 1 axpy, 2 ladder (A = T, B = L, C = R)
     double alpha, beta;
     Tensor *A, *B, *C;
     std::string ia, ib, ic;
@@ -192,6 +204,26 @@ class Engine {
                       uint8_t** cursor);
   void tc_contract(const GemmProb* probs, int np, const Mat& mp,
                    const Mat& mq, double alpha, double beta, double fl);
+  const char* run_gemms(const GemmProb* probs, int np, const Mat& mp,
+                        const Mat& mq, double alpha, double beta);
+
+  // on-the-fly ladder
+  struct LadBatch {
+    int G, ga, a0, a1;   // pair irrep, irrep of a, a range (local indices)
+    int64_t rows;        // (a,b) rows = (a1 - a0) * n_v(ga ^ G)
+  };
+  std::vector<LadBatch> ladder_batches(const Layout& TL);
+  double ladder_build(const LadBatch& b, Tensor* L);   // -> lad_w_
+  void ladder_perm(const LadBatch& b, bool inverse, const double* src,
+                   double* dst);
+  void ladder_apply_batch(const LadBatch& b, double alpha, Tensor* X,
+                          Tensor* Y);
+  void ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
+                      Tensor* dT, Tensor* dL);
+  void ladder_reserve(int64_t n);
+  double* lad_x_ = nullptr;
+  double* lad_w_ = nullptr;
+  int64_t lad_n_ = 0;
 
   Tensor* new_tensor(const std::string& name, std::vector<int> spaces,
                      int split, int gtot);

@@ -241,7 +241,10 @@ bool is_thin(const GemmProb& g) {
 }
 
 int64_t thin_chunk(const GemmProb& g) {
-  return std::max<int64_t>(4096, (g.K + 4 * SMS - 1) / (4 * SMS));
+  // about four CTAs per SM over all thin products of a launch, at least
+  // four k per thread
+  const int64_t kc = std::max<int64_t>(1024, (g.K + 4 * SMS - 1) / (4 * SMS));
+  return (kc + 255) / 256 * 256;
 }
 
 int thin_blocks(const GemmProb& g) {
@@ -249,27 +252,66 @@ int thin_blocks(const GemmProb& g) {
   return (int)((g.K + kc - 1) / kc);
 }
 
+constexpr int THIN_OT = 16;   // outputs accumulated per pass in registers
+
+struct ThinLaunch {
+  GemmProb p[GEMM_MAXPROB];
+  int first[GEMM_MAXPROB + 1];   // first CTA of each product
+  int64_t kc[GEMM_MAXPROB];
+  int64_t poff[GEMM_MAXPROB];    // partial sums of product i at part+poff
+  int np;
+};
+
+// One launch for all thin products: CTA b owns one K chunk of one product
+// and writes the partial sums of all its M*N outputs (fixed-order block
+// reduction); splitk_reduce_kernel adds the chunks in order.
 __global__ void __launch_bounds__(256)
-    thin_kernel(const GemmProb P, int64_t kc, double* __restrict__ part) {
-  __shared__ double red[8];
-  const int64_t k0 = (int64_t)blockIdx.x * kc;
-  const int64_t k1 = min((int64_t)P.K, k0 + kc);
-  for (int o = 0; o < P.M * P.N; ++o) {
-    const int m = o / P.N, n = o % P.N;
-    double acc = 0.0;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
-      const double a = P.ta ? P.A[k * P.lda + m] : P.A[(int64_t)m * P.lda + k];
-      const double b = P.tb ? P.B[(int64_t)n * P.ldb + k] : P.B[k * P.ldb + n];
-      acc = fma(a, b, acc);
+    thin_kernel(const __grid_constant__ ThinLaunch T,
+                double* __restrict__ part) {
+  __shared__ double red[8][THIN_OT];
+  int i = 0;
+  while (i + 1 < T.np && (int)blockIdx.x >= T.first[i + 1]) ++i;
+  const GemmProb& P = T.p[i];
+  const int blk = (int)blockIdx.x - T.first[i];
+  const int64_t k0 = (int64_t)blk * T.kc[i];
+  const int64_t k1 = min((int64_t)P.K, k0 + T.kc[i]);
+  const int MN = P.M * P.N;
+  double* out = part + T.poff[i] + (int64_t)blk * MN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o0 = 0; o0 < MN; o0 += THIN_OT) {
+    const int no = min(THIN_OT, MN - o0);
+    int mq[THIN_OT], nq[THIN_OT];
+    double acc[THIN_OT];
+#pragma unroll
+    for (int q = 0; q < THIN_OT; ++q) {
+      const int o = o0 + min(q, no - 1);
+      mq[q] = o / P.N;
+      nq[q] = o - mq[q] * P.N;
+      acc[q] = 0.0;
     }
-    for (int s = 16; s > 0; s >>= 1)
-      acc += __shfl_down_sync(0xffffffffu, acc, s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += 256) {
+#pragma unroll
+      for (int q = 0; q < THIN_OT; ++q) {
+        if (q < no) {
+          const double a = P.ta ? P.A[k * P.lda + mq[q]]
+                                : P.A[(int64_t)mq[q] * P.lda + k];
+          const double b = P.tb ? P.B[(int64_t)nq[q] * P.ldb + k]
+                                : P.B[k * P.ldb + nq[q]];
+          acc[q] = fma(a, b, acc[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < THIN_OT; ++q) {
+      double v = acc[q];
+      for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xffffffffu, v, s);
+      if (lane == 0) red[warp][q] = v;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < no) {
       double t = 0.0;
-      for (int w = 0; w < 8; ++w) t += red[w];
-      part[((int64_t)blockIdx.x * P.M + m) * P.N + n] = t;
+      for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+      out[o0 + threadIdx.x] = t;
     }
     __syncthreads();
   }
@@ -318,11 +360,17 @@ int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
   R.beta = beta;
   R.scratch = tpart;
   int64_t off = 0, relem = 0;
+  ThinLaunch T;
+  std::memset(&T, 0, sizeof(T));
+  int nblk = 0;
   for (int i = 0; i < nt; ++i) {
     const GemmProb& g = thin[i];
     const int nb = thin_blocks(g);
-    thin_kernel<<<nb, 256, 0, st>>>(g, thin_chunk(g), tpart + off);
-    ++launches;
+    T.p[i] = g;
+    T.first[i] = nblk;
+    T.kc[i] = thin_chunk(g);
+    T.poff[i] = off;
+    nblk += nb;
     R.C[i] = g.C;
     R.M[i] = g.M;
     R.N[i] = g.N;
@@ -333,6 +381,10 @@ int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
     relem += (int64_t)g.M * g.N;
     off += (int64_t)nb * g.M * g.N;
   }
+  T.first[nt] = nblk;
+  T.np = nt;
+  thin_kernel<<<nblk, 256, 0, st>>>(T, tpart);
+  ++launches;
   R.np = nt;
   R.elem0[nt] = relem;
   splitk_reduce_kernel<<<1, 256, 0, st>>>(R);

@@ -1,0 +1,395 @@
+// ladder.cu -- particle-particle ladder with the (ab|cd) integrals assembled
+// on the fly from the virtual-virtual Cholesky vectors (Sec. 2.3).
+//
+// For the pair irrep G the ladder is the product R_G[(ij),(ab)] +=
+// T_G[(ij),(cd)] W_G[(ab),(cd)]^T with W[a,b,c,d] = (ac|bd) =
+// sum_P L[P,a,c] L[P,b,d].  W_G is symmetric (every L^P is), so it is built
+// one row batch at a time: the rows (a,b) with a in [a0,a1) of irrep ga and
+// b of irrep gb = ga^G.  For each irrep gc of c (gd = gc^G, the Cholesky
+// irrep is Gp = ga^gc) one GEMM over P gives
+//     X_gc[(a,c),(b,d)] = sum_P L_Gp[P,(a,c)] L_Gp[P,(b,d)],
+// all gc in one grouped launch; a permutation writes the batch rows
+// W[(a,b),(c,d)], and one GEMM applies them.  Peak memory is two batches
+// instead of sum_G N_vv(G)^2 doubles.
+//
+// Adjoint (Lambda iterations and the density sweep), with dR the adjoint of R:
+//   dT_G[(ij),(cd) in batch] += dR_G[(ij),(ab)] W[(ab),(cd) in batch]
+//        = dR_G W_batch^T                      (W symmetric: same as forward)
+//   dW_batch[(ab),(cd)] = sum_ij dR_G[ij,(ab) in batch] T_G[ij,(cd)]
+//   dL[P,a,c] += sum_bd dW[a,b,c,d] L[P,b,d],  dL[P,b,d] += sum_ac dW[a,b,c,d]
+//        L[P,a,c]                              (two launches: their targets
+//                                               overlap when ga == gb)
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+
+#include "engine.h"
+
+namespace cdcc {
+
+#define LCK(x)                                                            \
+  do {                                                                    \
+    cudaError_t e_ = (x);                                                 \
+    if (e_ != cudaSuccess)                                                \
+      throw EngineError(std::string("CUDA: ") + cudaGetErrorString(e_) + \
+                        " at " #x);                                       \
+  } while (0)
+
+namespace {
+
+bool is_doubles(const Layout& L) {
+  return L.rank == 4 && L.split == 2 && L.gtot == 0 && L.sp[0] == SO &&
+         L.sp[1] == SO && L.sp[2] == SV && L.sp[3] == SV;
+}
+
+bool is_lvv(const Layout& L) {
+  return L.rank == 3 && L.split == 1 && L.gtot == 0 && L.sp[0] == SQ &&
+         L.sp[1] == SV && L.sp[2] == SV;
+}
+
+void check_block(const GemmProb& g, const double* a0, int64_t asz,
+                 const double* b0, int64_t bsz, const double* c0,
+                 int64_t csz) {
+  // last element touched by each operand (row-major blocks with leading
+  // dimensions lda/ldb/ldc; ta/tb swap the stored shape)
+  const int64_t ar = g.ta ? g.K : g.M, ac = g.ta ? g.M : g.K;
+  const int64_t br = g.tb ? g.N : g.K, bc = g.tb ? g.K : g.N;
+  const int64_t ea = (g.A - a0) + (ar - 1) * g.lda + ac;
+  const int64_t eb = (g.B - b0) + (br - 1) * g.ldb + bc;
+  const int64_t ec = (g.C - c0) + (int64_t)(g.M - 1) * g.ldc + g.N;
+  if (g.A < a0 || g.B < b0 || g.C < c0 || ea > asz || eb > bsz || ec > csz ||
+      ac > g.lda || bc > g.ldb || g.N > g.ldc)
+    throw EngineError("internal: ladder GEMM block out of bounds");
+}
+
+}  // namespace
+
+std::vector<Engine::LadBatch> Engine::ladder_batches(const Layout& TL) {
+  std::vector<LadBatch> out;
+  const int h = dims_.h;
+  for (int G = 0; G < h; ++G) {
+    const int64_t ncol = TL.ncol[G];
+    if (ncol == 0 || TL.nrow[G] == 0) continue;
+    const int64_t max_rows =
+        std::max<int64_t>(1, ladder_batch_bytes / (8 * ncol));
+    for (int ga = 0; ga < h; ++ga) {
+      const int gb = ga ^ G;
+      const int na = dims_.n[SV][ga], nb = dims_.n[SV][gb];
+      if (na == 0 || nb == 0) continue;
+      const int step = (int)std::max<int64_t>(
+          1, std::min<int64_t>(na, max_rows / nb));
+      for (int a0 = 0; a0 < na; a0 += step) {
+        const int a1 = std::min(na, a0 + step);
+        out.push_back({G, ga, a0, a1, (int64_t)(a1 - a0) * nb});
+      }
+    }
+  }
+  return out;
+}
+
+void Engine::ladder_reserve(int64_t n) {
+  if (n <= lad_n_) return;
+  if (lad_x_) al.release(lad_x_, (size_t)lad_n_ * 8);
+  if (lad_w_) al.release(lad_w_, (size_t)lad_n_ * 8);
+  lad_x_ = lad_w_ = nullptr;
+  lad_n_ = 0;
+  lad_x_ = (double*)al.alloc((size_t)n * 8);
+  lad_w_ = (double*)al.alloc((size_t)n * 8);
+  lad_n_ = n;
+}
+
+// X_gc blocks of one batch: [a][c][b][d] for gc = 0..h-1, back to back.
+// forward: lad_x_ -> W rows [(a,b)][(c,d)] (leading dimension N_vv(G));
+// inverse: the same boxes read from W and written to X.
+void Engine::ladder_perm(const LadBatch& b, bool inverse, const double* src,
+                         double* dst) {
+  const int h = dims_.h, G = b.G;
+  // column offsets of the (c,d) sub-blocks of irrep pair G (same order as
+  // the column group of a {SO,SO,SV,SV} / {SV,SV,SV,SV} layout)
+  int64_t ncol = 0;
+  std::vector<int64_t> coff(h);
+  for (int gc = 0; gc < h; ++gc) {
+    coff[gc] = ncol;
+    ncol += (int64_t)dims_.n[SV][gc] * dims_.n[SV][gc ^ G];
+  }
+  std::ostringstream key;
+  key << "ladder:" << b.G << ':' << b.ga << ':' << b.a0 << ':' << b.a1
+      << (inverse ? 'i' : 'f');
+  auto it = task_cache_.find(key.str());
+  if (it == task_cache_.end()) {
+    const int ga = b.ga, gb = ga ^ G;
+    const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
+    std::vector<PermTask> tasks;
+    int64_t xoff = 0;
+    for (int gc = 0; gc < h; ++gc) {
+      const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gc ^ G];
+      const int64_t xsz = (int64_t)na * nc * nb * nd;
+      if (xsz > 0) {
+        PermTask t;
+        std::memset(&t, 0, sizeof(t));
+        t.rank = 4;
+        // box index order (a, b, c, d); W side and X side offsets
+        const int64_t wbase = coff[gc];
+        const int64_t ws[4] = {(int64_t)nb * ncol, ncol, nd, 1};
+        const int64_t xs[4] = {(int64_t)nc * nb * nd, nd, (int64_t)nb * nd, 1};
+        t.dim[0] = na;
+        t.dim[1] = nb;
+        t.dim[2] = nc;
+        t.dim[3] = nd;
+        for (int q = 0; q < 4; ++q) {
+          t.ys[q] = inverse ? xs[q] : ws[q];
+          t.xs[q] = inverse ? ws[q] : xs[q];
+        }
+        t.ybase = inverse ? xoff : wbase;
+        t.xbase = inverse ? wbase : xoff;
+        t.n = xsz;
+        // both boxes inside the batch buffers (last W element touched:
+        // row na*nb - 1, column coff + nc*nd - 1)
+        const int64_t wend = (int64_t)(na * nb - 1) * ncol + wbase +
+                             (int64_t)nc * nd;
+        if (xoff + xsz > b.rows * ncol || wend > b.rows * ncol ||
+            b.rows * ncol > lad_n_)
+          throw EngineError("internal: ladder permutation out of bounds");
+        tasks.push_back(t);
+      }
+      xoff += xsz;
+    }
+    if (xoff != b.rows * ncol)
+      throw EngineError("internal: ladder batch size mismatch");
+    std::vector<Chunk> chunks;
+    const int CH = chunk_elems();
+    for (int i = 0; i < (int)tasks.size(); ++i)
+      for (int64_t s = 0; s < tasks[i].n; s += CH) chunks.push_back({i, s});
+    DevTasks dt;
+    dt.ntask = (int)tasks.size();
+    dt.nchunk = (int)chunks.size();
+    if (dt.ntask) {
+      dt.tasks = (PermTask*)al.alloc(tasks.size() * sizeof(PermTask));
+      dt.chunks = (Chunk*)al.alloc(chunks.size() * sizeof(Chunk));
+      LCK(cudaMemcpyAsync(dt.tasks, tasks.data(),
+                          tasks.size() * sizeof(PermTask),
+                          cudaMemcpyHostToDevice, st_));
+      LCK(cudaMemcpyAsync(dt.chunks, chunks.data(),
+                          chunks.size() * sizeof(Chunk),
+                          cudaMemcpyHostToDevice, st_));
+      LCK(cudaStreamSynchronize(st_));
+    }
+    it = task_cache_.emplace(key.str(), dt).first;
+  }
+  const DevTasks& dt = it->second;
+  timed(K_PERM, 16.0 * (double)b.rows * ncol, [&] {
+    return perm_axpy(dt.tasks, dt.chunks, dt.nchunk, 1.0, src, 0.0, dst, st_);
+  });
+}
+
+// W rows of batch b into lad_w_ (via lad_x_); returns the GEMM flops.
+double Engine::ladder_build(const LadBatch& b, Tensor* L) {
+  const int h = dims_.h, G = b.G, ga = b.ga, gb = ga ^ G;
+  const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
+  const Layout& LL = L->lay;
+  GemmProb probs[GEMM_MAXPROB];
+  int np = 0;
+  int64_t xoff = 0;
+  bool holes = false;
+  for (int gc = 0; gc < h; ++gc) {
+    const int gd = gc ^ G, Gp = ga ^ gc;
+    const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gd];
+    const int64_t M = (int64_t)na * nc, N = (int64_t)nb * nd;
+    const int64_t K = LL.nrow[Gp];
+    if (M * N == 0) continue;
+    if (K == 0) {
+      holes = true;          // (ac|bd) = 0 for an empty Cholesky irrep
+      xoff += M * N;
+      continue;
+    }
+    const int64_t ld = LL.ncol[Gp];
+    GemmProb g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = L->d + LL.blk_off[Gp] + LL.csub[Gp * LL.ncode_c + ga] +
+          (int64_t)b.a0 * nc;
+    g.ta = 1;
+    g.lda = (int)ld;
+    g.B = L->d + LL.blk_off[Gp] + LL.csub[Gp * LL.ncode_c + gb];
+    g.tb = 0;
+    g.ldb = (int)ld;
+    g.C = lad_x_ + xoff;
+    g.ldc = (int)N;
+    g.M = (int)M;
+    g.N = (int)N;
+    g.K = (int)K;
+    check_block(g, L->d, LL.size, L->d, LL.size, lad_x_, lad_n_);
+    probs[np++] = g;
+    xoff += M * N;
+  }
+  if (holes) LCK(cudaMemsetAsync(lad_x_, 0, (size_t)xoff * 8, st_));
+  double fl = 0;
+  if (np > 0) {
+    const Mat ml{L->d, &LL, false, L};
+    run_gemms(probs, np, ml, ml, 1.0, 0.0);
+    for (int i = 0; i < np; ++i)
+      fl += 2.0 * probs[i].M * (double)probs[i].N * probs[i].K;
+  }
+  ladder_perm(b, false, lad_x_, lad_w_);
+  return fl;
+}
+
+// Y_G[(ij), (ab) in batch] += alpha * X_G[(ij),(cd)] W_batch^T
+void Engine::ladder_apply_batch(const LadBatch& b, double alpha, Tensor* X,
+                                Tensor* Y) {
+  const Layout& XL = X->lay;
+  const int G = b.G;
+  const int64_t M = XL.nrow[G], K = XL.ncol[G];
+  if (M == 0) return;
+  const int gb = b.ga ^ G;
+  GemmProb g;
+  std::memset(&g, 0, sizeof(g));
+  g.A = X->d + XL.blk_off[G];
+  g.lda = (int)K;
+  g.B = lad_w_;
+  g.tb = 1;
+  g.ldb = (int)K;
+  g.C = Y->d + Y->lay.blk_off[G] + Y->lay.csub[G * Y->lay.ncode_c + b.ga] +
+        (int64_t)b.a0 * dims_.n[SV][gb];
+  g.ldc = (int)K;
+  g.M = (int)M;
+  g.N = (int)b.rows;
+  g.K = (int)K;
+  check_block(g, X->d, XL.size, lad_w_, lad_n_, Y->d, Y->lay.size);
+  const Mat mx{X->d, &XL, false, X};
+  const Mat mw{lad_w_, nullptr, false, nullptr};
+  run_gemms(&g, 1, mx, mw, alpha, 1.0);
+}
+
+void Engine::ladder(double alpha, Tensor* T, Tensor* L, Tensor* R) {
+  if (!is_doubles(T->lay) || !is_doubles(R->lay) || !is_lvv(L->lay))
+    throw EngineError("ladder: layouts must be {SO,SO,SV,SV}/2 and "
+                      "{SQ,SV,SV}/1");
+  if (recording_)
+    tape_.push_back({2, alpha, 1.0, T, L, R, "ijcd", "Pac", "ijab"});
+  if (record_only_) return;
+  ++R->ver;
+  cudaEvent_t tr_a = nullptr;
+  if (prof_on_) {
+    tr_a = get_event();
+    cudaEventRecord(tr_a, st_);
+  }
+  const std::vector<LadBatch> bs = ladder_batches(T->lay);
+  int64_t need = 0;
+  for (const LadBatch& b : bs)
+    need = std::max(need, b.rows * T->lay.ncol[b.G]);
+  ladder_reserve(need);
+  double fl = 0;
+  for (const LadBatch& b : bs) {
+    fl += ladder_build(b, L);
+    ladder_apply_batch(b, alpha, T, R);
+    fl += 2.0 * (double)b.rows * T->lay.ncol[b.G] * T->lay.nrow[b.G];
+  }
+  if (tr_a) {
+    cudaEvent_t tr_b = get_event();
+    cudaEventRecord(tr_b, st_);
+    trace_pending_.push_back({"ladder on the fly (ijcd,Pac,Pbd->ijab)", tr_a,
+                              tr_b, fl});
+  }
+  release_scratch();
+}
+
+void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
+                            Tensor* dT, Tensor* dL) {
+  if (!dT && !dL) return;
+  const std::vector<LadBatch> bs = ladder_batches(T->lay);
+  int64_t need = 0;
+  for (const LadBatch& b : bs)
+    need = std::max(need, b.rows * T->lay.ncol[b.G]);
+  ladder_reserve(need);
+  const int h = dims_.h;
+  const Layout& LL = L->lay;
+  for (const LadBatch& b : bs) {
+    ladder_build(b, L);
+    if (dT) ladder_apply_batch(b, alpha, dR, dT);
+    if (!dL) continue;
+    const int G = b.G, ga = b.ga, gb = ga ^ G;
+    const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
+    const Layout& RL = dR->lay;
+    const int64_t K = RL.nrow[G], ncol = RL.ncol[G];
+    if (K == 0) continue;
+    // dW_batch = alpha * dR_G[:, batch]^T T_G  -> lad_w_
+    {
+      GemmProb g;
+      std::memset(&g, 0, sizeof(g));
+      g.A = dR->d + RL.blk_off[G] + RL.csub[G * RL.ncode_c + ga] +
+            (int64_t)b.a0 * nb;
+      g.ta = 1;
+      g.lda = (int)ncol;
+      g.B = T->d + T->lay.blk_off[G];
+      g.ldb = (int)ncol;
+      g.C = lad_w_;
+      g.ldc = (int)ncol;
+      g.M = (int)b.rows;
+      g.N = (int)ncol;
+      g.K = (int)K;
+      check_block(g, dR->d, RL.size, T->d, T->lay.size, lad_w_, lad_n_);
+      const Mat ma{dR->d, &RL, false, dR};
+      const Mat mb{T->d, &T->lay, false, T};
+      run_gemms(&g, 1, ma, mb, alpha, 0.0);
+    }
+    ladder_perm(b, true, lad_w_, lad_x_);        // dX_gc[(a,c),(b,d)]
+    GemmProb p1[GEMM_MAXPROB], p2[GEMM_MAXPROB];
+    int n1 = 0, n2 = 0;
+    int64_t xoff = 0;
+    for (int gc = 0; gc < h; ++gc) {
+      const int gd = gc ^ G, Gp = ga ^ gc;
+      const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gd];
+      const int64_t MA = (int64_t)na * nc, NB = (int64_t)nb * nd;
+      const int64_t P = LL.nrow[Gp], ld = LL.ncol[Gp];
+      if (MA * NB == 0) continue;
+      if (P == 0) {
+        xoff += MA * NB;
+        continue;
+      }
+      double* LA = L->d + LL.blk_off[Gp] + LL.csub[Gp * LL.ncode_c + ga] +
+                   (int64_t)b.a0 * nc;
+      double* LB = L->d + LL.blk_off[Gp] + LL.csub[Gp * LL.ncode_c + gb];
+      const int64_t oA = LA - L->d, oB = LB - L->d;
+      // dL_A[P,(ac)] += L_B[P,(bd)] dX[(ac),(bd)]^T
+      GemmProb g1;
+      std::memset(&g1, 0, sizeof(g1));
+      g1.A = LB;
+      g1.lda = (int)ld;
+      g1.B = lad_x_ + xoff;
+      g1.tb = 1;
+      g1.ldb = (int)NB;
+      g1.C = dL->d + oA;
+      g1.ldc = (int)ld;
+      g1.M = (int)P;
+      g1.N = (int)MA;
+      g1.K = (int)NB;
+      check_block(g1, L->d, LL.size, lad_x_, lad_n_, dL->d, dL->lay.size);
+      p1[n1++] = g1;
+      // dL_B[P,(bd)] += L_A[P,(ac)] dX[(ac),(bd)]
+      GemmProb g2;
+      std::memset(&g2, 0, sizeof(g2));
+      g2.A = LA;
+      g2.lda = (int)ld;
+      g2.B = lad_x_ + xoff;
+      g2.tb = 0;
+      g2.ldb = (int)NB;
+      g2.C = dL->d + oB;
+      g2.ldc = (int)ld;
+      g2.M = (int)P;
+      g2.N = (int)NB;
+      g2.K = (int)MA;
+      check_block(g2, L->d, LL.size, lad_x_, lad_n_, dL->d, dL->lay.size);
+      p2[n2++] = g2;
+      xoff += MA * NB;
+    }
+    const Mat ml{L->d, &LL, false, L};
+    const Mat mx{lad_x_, nullptr, false, nullptr};
+    if (n1) run_gemms(p1, n1, ml, mx, 1.0, 1.0);
+    if (n2) run_gemms(p2, n2, ml, mx, 1.0, 1.0);
+  }
+  if (dT) ++dT->ver;
+  if (dL) ++dL->ver;
+  release_scratch();
+}
+
+}  // namespace cdcc

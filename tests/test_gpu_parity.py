@@ -119,6 +119,17 @@ def test_nontotally_symmetric_displacements_vanish(cd):
     assert g[1] == 0.0 and abs(g[0] - g[2]) < 1e-14 and g[0] != 0.0
 
 
+def test_bounded_wait_gives_up_and_device_stays_usable(cd):
+    """Failure detection without a GPU fault: a wait that nothing completes
+    runs out, is reported as CDCC_ETIMEOUT, and work continues."""
+    assert cd.cdcc_selftest_bounded_wait() == cd.CDCC_ETIMEOUT
+    s = random_system([1], [2], [3], seed=19, scale=0.4)
+    ctx = cd.init_from_system(s)
+    e, g = cd.gradient(ctx, make_displacements(s, 1))
+    cd.cd_ccsd_free(ctx)
+    assert np.isfinite(e) and np.all(np.isfinite(g))
+
+
 def test_call_order_enforced(cd):
     s = random_system([1], [2], [3], seed=9, scale=0.4)
     ctx = cd.init_from_system(s)
