@@ -49,6 +49,11 @@ def parse():
                     help="other schedules to time beside --precision: "
                          "'all', 'none' or a comma list")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--serving", action="store_true",
+                    help="run the serving workload (Poisson arrivals of "
+                         "mixed requests) instead of a fixed workload")
+    ap.add_argument("--jobs", type=int, default=64)
+    ap.add_argument("--slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -226,6 +231,7 @@ def run_ours(args, rank, ws):
         stats = None
         if profile:
             stats = [cdcc.cdcc_kernel_stats(ctx, k) for k in range(6)]
+            stats.append(cdcc.cdcc_ladder_stats(ctx))
         nl = cdcc.cdcc_kernel_launches(ctx)
         ph = cdcc.cdcc_phase_times(ctx)
         cdcc.cd_ccsd_free(ctx)
@@ -241,7 +247,7 @@ def run_ours(args, rank, ws):
     barrier(ws)
     torch.cuda.synchronize()
     times, launches = [], 0
-    agg = np.zeros((6, 3))
+    agg = np.zeros((7, 3))
     for _ in range(args.steps):
         flush.fill_(1.0)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -278,13 +284,16 @@ def run_ours(args, rank, ws):
             torch.cuda.synchronize()
             o_times.append(ev0.elapsed_time(ev1) * 1e-3)
         tc = o_stats[5]
+        lad = o_stats[6]
         other_lines.append({
             "precision": other,
             "time_to_gradient_s": float(np.median(o_times)),
             "abs_dE_vs_this_run": abs(o_e - e),
             "max_abs_dg_vs_this_run": float(np.abs(o_g - g).max()),
             "tc_gemm_s": tc[0],
-            "tc_gemm_tflops": tc[2] / tc[0] / 1e12 if tc[0] > 0 else None})
+            "tc_gemm_tflops": tc[2] / tc[0] / 1e12 if tc[0] > 0 else None,
+            "ladder_s": lad[0],
+            "ladder_tflops": lad[1] / lad[0] / 1e12 if lad[0] > 0 else None})
     args.precision = saved
 
     # ---- end to end through the C ABI with host buffers
@@ -334,6 +343,13 @@ def run_ours(args, rank, ws):
         "phases_s": {"ccsd": ph[0], "lambda": ph[1], "density": ph[2],
                      "contract_dL": ph[3]},
         "kernel_classes": classes,
+        "ladder": {"seconds_per_step": agg[6][0] / args.steps,
+                   "flops_per_step": agg[6][1] / args.steps,
+                   "tflops": (agg[6][1] / agg[6][0] / 1e12
+                              if agg[6][0] > 0 else None),
+                   "share_of_step": agg[6][0] / args.steps / t50,
+                   "note": "algorithmic flops of the ladder products, "
+                           "(ac|bd) builds and their adjoints"},
         "roofline": {"kernel": "gemm64_kernel (FP64 DFMA grouped GEMM)",
                      "bound": "alu", "achieved": achieved / 1e3,
                      "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
@@ -350,11 +366,94 @@ def run_ours(args, rank, ws):
     print(json.dumps(out), flush=True)
 
 
+def run_serving(args, rank, ws):
+    """Serving workload: requests arrive as a Poisson stream (mean 0.5 s),
+    are admitted by device memory and slots, overlap on the GPU and report
+    p50 / p99 time-to-gradient (completion - arrival) and jobs/s.  Each
+    replica (N > 1) serves the whole stream on its own GPU."""
+    import torch
+    from synth import make_displacements
+    from synth.serving import serving_jobs, job_system
+    from paper_2512_21909_gb300 import build as cbuild, cdcc
+    from paper_2512_21909_gb300.serve import (GradientServer, Request,
+                                              latency_stats)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        cbuild.build()
+    barrier(ws)
+    prec = {"fp64": cdcc.PREC_FP64, "mixed": cdcc.PREC_MIXED,
+            "tc": cdcc.PREC_TC}[args.precision]
+    specs = serving_jobs()[:args.jobs]
+    reqs = []
+    for sp in specs:
+        sysm = job_system(sp)
+        reqs.append(Request.from_system(sp.index, sp.arrival, sysm,
+                                        make_displacements(sysm, 2)))
+        reqs[-1].extra.update(group=sp.group, o=sp.o)
+    # warm-up: the smallest request alone
+    small = min(specs, key=lambda j: j.o)
+    ws_sys = job_system(small)
+    warm = [Request.from_system(-1, 0.0, ws_sys,
+                                make_displacements(ws_sys, 2))]
+    srv = GradientServer(device=dev, precision=prec, max_active=args.slots)
+    for _ in range(max(1, args.warmup)):
+        srv.run([Request.from_system(-1, 0.0, ws_sys, warm[0].dL)],
+                realtime=False)
+    clk = ClockSampler(dev)
+    clk.start()
+    barrier(ws)
+    srv.run(reqs, realtime=True)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.stop()
+    st = latency_stats(reqs, srv.wall)
+    p50 = allmax(st["p50_s"] or float("nan"), ws)
+    p99 = allmax(st["p99_s"] or float("nan"), ws)
+    wall = allmax(srv.wall, ws)
+    if rank != 0:
+        return
+    h2d = sum(r.L.nbytes + r.dL.nbytes for r in reqs)
+    out = {
+        "metric": "serving: time-to-gradient p50 (p99 and jobs/s beside) "
+                  "under Poisson arrivals",
+        "value": p50, "unit": "s", "n_gpus": ws, "steps": 1,
+        "warmup": max(1, args.warmup), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "bf16x3+f64",
+                  "tc": "bf16x3+exact-slice"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"c4: {len(reqs)} requests, Poisson arrivals "
+                               "mean 0.5 s, o~U{4..40}, v=9o, nL=40o, "
+                               "C1/C2v/D2h, 2 displacements each",
+                   "precision": args.precision, "slots": args.slots,
+                   "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "p50_s": p50, "p99_s": p99,
+        "jobs_per_s": ws * len(reqs) / wall if wall > 0 else None,
+        "done": st["done"], "failed": st["failed"], "wall_s": wall,
+        "max_concurrent": srv.max_seen_active,
+        "e2e": {"value": p50, "unit": "s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(sum(8 * (r.dL.shape[0] + 1)
+                                              for r in reqs))},
+        "requests": [{"i": r.index, "group": r.extra["group"],
+                      "o": r.extra["o"], "latency_s": r.latency,
+                      "admit_s": (r.t_admit - r.arrival
+                                  if r.t_admit is not None else None),
+                      "ladder": "stored" if r.ladder == cdcc.LADDER_STORED
+                      else "otf", "status": r.status, "e_corr": r.e}
+                     for r in reqs],
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, ws = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, ws)
+    elif args.serving:
+        run_serving(args, rank, ws)
     else:
         run_ours(args, rank, ws)
     from paper_2512_21909_gb300 import replicas

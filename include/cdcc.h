@@ -232,6 +232,13 @@ cdcc_status cdcc_solver_info(cdcc_ctx *ctx, int *info);
 /* The ladder mode the context chose (CDCC_LADDER_STORED or _OTF).         */
 cdcc_status cdcc_ladder_mode(cdcc_ctx *ctx, int *mode);
 
+/* Particle-particle ladder work since profiling was enabled (cdcc_profile):
+ * device seconds, algorithmic flops (sum over the ladder products, their
+ * adjoints, the (ac|bd) builds from L^P_ab and their adjoints) and calls.
+ * Zero while profiling is off.                                            */
+cdcc_status cdcc_ladder_stats(cdcc_ctx *ctx, double *seconds, double *flops,
+                              long long *calls);
+
 /*
  * C = beta*C + alpha * op(A) op(B) on device buffers, row-major, with the
  * library's contraction kernels (the building block of every contraction of

@@ -5,6 +5,8 @@ o^2 v^2 nL; s_cfg rescales L (and dL) so that E_MP2 is about -0.04 Eh per
 occupied orbital.  E_MP2 is homogeneous of degree 4 in L, hence
     s_cfg = min(1, (0.04 o / |E_MP2(s=1)|)^(1/4)).
 Run:  python -m oracle.calibrate_scale   (prints the table)
+      python -m oracle.calibrate_scale --serving   (writes
+      synth/serving_scales.json, the per-request scales of the serving workload)
 """
 from __future__ import annotations
 
@@ -56,7 +58,26 @@ def calibrate(idx: int) -> float:
     return min(1.0, (0.04 * s1.nocc / abs(e)) ** 0.25), e
 
 
+def calibrate_serving(path=None):
+    """Per-request scales of the serving workload -> synth/serving_scales.json
+    (same rule as the fixed workloads, E_MP2 from the arrays at s = 1)."""
+    import json
+    from synth.serving import serving_jobs, job_system, SCALES_FILE
+    out = {}
+    for spec in serving_jobs():
+        s1 = job_system(spec, scale=1.0)
+        e = mp2_chunked(s1.eps, _ov_dense(s1))
+        out[str(spec.index)] = min(1.0, (0.04 * s1.nocc / abs(e)) ** 0.25)
+        print(spec.index, spec.group, spec.o, out[str(spec.index)], flush=True)
+    with open(path or SCALES_FILE, "w") as f:
+        json.dump(out, f, indent=1)
+
+
 if __name__ == "__main__":
-    for idx in sorted(CONFIGS):
-        s, e = calibrate(idx)
-        print(f"{idx}: s_cfg = {s!r}   (E_MP2 at s=1: {e:.6e})")
+    import sys
+    if "--serving" in sys.argv:
+        calibrate_serving()
+    else:
+        for idx in sorted(CONFIGS):
+            s, e = calibrate(idx)
+            print(f"{idx}: s_cfg = {s!r}   (E_MP2 at s=1: {e:.6e})")

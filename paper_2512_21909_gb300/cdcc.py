@@ -307,6 +307,18 @@ def cdcc_solver_info(ctx):
     return tuple(int(x) for x in info)
 
 
+def cdcc_ladder_stats(ctx):
+    """(seconds, algorithmic flops, calls) of the ladder contractions while
+    profiling was on."""
+    lib = load()
+    lib.cdcc_ladder_stats.argtypes = [ctypes.c_void_p] * 4
+    lib.cdcc_ladder_stats.restype = ctypes.c_int
+    sec, fl, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+    _check(ctx, lib.cdcc_ladder_stats(ctx.handle, ctypes.byref(sec),
+                                      ctypes.byref(fl), ctypes.byref(n)))
+    return sec.value, fl.value, n.value
+
+
 def cdcc_ladder_mode(ctx) -> int:
     """LADDER_STORED or LADDER_OTF, as chosen by the context."""
     lib = load()

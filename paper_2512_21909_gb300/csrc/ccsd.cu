@@ -200,6 +200,7 @@ void prepare(cdcc_ctx* c) {
   // W0[(ab),(cd)] = (ac|bd) is a symmetric matrix per block
   c->W0->symmetric = true;
   c->W0->constant = true;
+  c->W0->ladder = true;
 }
 
 // ------------------------------------------------------------------ residual
@@ -1137,6 +1138,16 @@ cdcc_status cdcc_kernel_stats(cdcc_ctx* c, int kind, double* seconds,
     if (seconds) *seconds = c->eng->prof_sec[kind];
     if (launches) *launches = (long long)c->eng->prof_n[kind];
     if (work) *work = c->eng->prof_work[kind];
+  });
+}
+
+cdcc_status cdcc_ladder_stats(cdcc_ctx* c, double* seconds, double* flops,
+                              long long* calls) {
+  if (!c || !c->eng || !seconds || !flops || !calls) return CDCC_EINVAL;
+  return guarded(c, [&] {
+    int64_t n = 0;
+    c->eng->ladder_stats(seconds, flops, &n);
+    *calls = (long long)n;
   });
 }
 

@@ -162,6 +162,7 @@ Tensor* Engine::adjoint(Tensor* t) {
     std::vector<int> sp(t->lay.sp, t->lay.sp + t->lay.rank);
     t->adj = tensor(t->name + "~", sp, t->lay.split, t->lay.gtot);
   }
+  t->adj->ladder = t->ladder;
   return t->adj;
 }
 
@@ -177,7 +178,7 @@ cudaEvent_t Engine::get_event() {
 }
 
 void Engine::prof_collect() {
-  if (pending_.empty()) return;
+  if (pending_.empty() && trace_pending_.empty()) return;
   ECK(cudaStreamSynchronize(st_));
   for (auto& r : pending_) {
     float ms = 0;
@@ -572,6 +573,7 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
     cudaEvent_t tr_b = get_event();
     cudaEventRecord(tr_b, st_);
     std::ostringstream key;
+    if (A->ladder || B->ladder || C->ladder) key << "ladder ";
     key << ia << ',' << ib << "->" << ic << " [" << path << ']';
     trace_pending_.push_back({key.str(), tr_a, tr_b, fl});
   }
@@ -621,6 +623,18 @@ const char* Engine::run_gemms(const GemmProb* probs, int np, const Mat& mp,
     });
   }
   return path;
+}
+
+void Engine::ladder_stats(double* sec, double* fl, int64_t* calls) {
+  prof_collect();
+  *sec = *fl = 0;
+  *calls = 0;
+  for (auto& kv : trace_)
+    if (kv.first.rfind("ladder", 0) == 0) {
+      *sec += kv.second.sec;
+      *fl += kv.second.flops;
+      *calls += kv.second.calls;
+    }
 }
 
 void Engine::write_trace(const char* file) {

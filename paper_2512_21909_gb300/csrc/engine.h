@@ -52,6 +52,9 @@ struct Tensor {
   bool symmetric = false;
   // amplitude independent: its tensor-core slices are cached per version
   bool constant = false;
+  // operand of the particle-particle ladder ((ac|bd) integrals and their
+  // adjoint): contractions touching it are timed as ladder work
+  bool ladder = false;
   uint64_t ver = 0;   // bumped on every write
 };
 
@@ -160,6 +163,9 @@ class Engine {
   void prof_collect();
   // append the per-contraction trace (profiling on) to `file`
   void write_trace(const char* file);
+  // device seconds, algorithmic flops and calls of the ladder contractions
+  // (profiling on): forward, adjoint, integral build and its adjoint
+  void ladder_stats(double* sec, double* flops, int64_t* calls);
   double prof_sec[K_NKIND] = {}, prof_work[K_NKIND] = {};
   int64_t prof_n[K_NKIND] = {};
 

@@ -296,6 +296,12 @@ void Engine::ladder(double alpha, Tensor* T, Tensor* L, Tensor* R) {
 void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
                             Tensor* dT, Tensor* dL) {
   if (!dT && !dL) return;
+  cudaEvent_t tr_a = nullptr;
+  if (prof_on_) {
+    tr_a = get_event();
+    cudaEventRecord(tr_a, st_);
+  }
+  double fl = 0;
   const std::vector<LadBatch> bs = ladder_batches(T->lay);
   int64_t need = 0;
   for (const LadBatch& b : bs)
@@ -304,9 +310,15 @@ void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
   const int h = dims_.h;
   const Layout& LL = L->lay;
   for (const LadBatch& b : bs) {
-    ladder_build(b, L);
-    if (dT) ladder_apply_batch(b, alpha, dR, dT);
+    fl += ladder_build(b, L);
+    const double fapply =
+        2.0 * (double)b.rows * T->lay.ncol[b.G] * T->lay.nrow[b.G];
+    if (dT) {
+      ladder_apply_batch(b, alpha, dR, dT);
+      fl += fapply;
+    }
     if (!dL) continue;
+    fl += 2.0 * fapply;   // dW and the two dL products (nominal)
     const int G = b.G, ga = b.ga, gb = ga ^ G;
     const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
     const Layout& RL = dR->lay;
@@ -389,6 +401,11 @@ void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
   }
   if (dT) ++dT->ver;
   if (dL) ++dL->ver;
+  if (tr_a) {
+    cudaEvent_t tr_b = get_event();
+    cudaEventRecord(tr_b, st_);
+    trace_pending_.push_back({"ladder on the fly, adjoint", tr_a, tr_b, fl});
+  }
   release_scratch();
 }
 
