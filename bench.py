@@ -342,6 +342,7 @@ def run_ours(args, rank, ws):
         "gpu_launches": int(launches / args.steps),
         "phases_s": {"ccsd": ph[0], "lambda": ph[1], "density": ph[2],
                      "contract_dL": ph[3]},
+        "peak_device_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
         "kernel_classes": classes,
         "ladder": {"seconds_per_step": agg[6][0] / args.steps,
                    "flops_per_step": agg[6][1] / args.steps,

@@ -600,7 +600,8 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
   bool early = mixed(c);
   SwitchRule sw(c->opt.switch_tol);
   c->iters_mixed[1] = c->iters_fp64[1] = 0;
-  diis_init(c, c->lam_diis, "lamdiis", c->lam->lay.size);
+  // the CCSD history is no longer needed: Lambda reuses its buffers
+  diis_init(c, c->lam_diis, "ccdiis", c->lam->lay.size);
   Tensor* g1 = e.adjoint(c->T1);
   Tensor* g2 = e.adjoint(c->T2);
   double rmax = 0;

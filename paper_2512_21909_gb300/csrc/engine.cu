@@ -209,6 +209,16 @@ void Engine::zero(Tensor* t) {
     ECK(cudaMemsetAsync(t->d, 0, (size_t)t->lay.size * 8, st_));
 }
 
+void Engine::set_precision(int slices) {
+  if (slices == tc_slices_) return;
+  tc_slices_ = slices;
+  for (auto& kv : slice_cache_) {
+    al.release(kv.second.data, kv.second.bytes);
+    if (kv.second.exps) al.release(kv.second.exps, kv.second.ebytes);
+  }
+  slice_cache_.clear();
+}
+
 double* Engine::scratch(int64_t n) {
   n = std::max<int64_t>(n, 1);
   int best = -1;
@@ -217,6 +227,16 @@ double* Engine::scratch(int64_t n) {
         (best < 0 || pool_[i].n < pool_[best].n))
       best = i;
   if (best < 0) {
+    // idle buffers too small for this request go back to the allocator, so
+    // the pool stays near the largest simultaneous need
+    std::vector<Buf> keep;
+    for (auto& b : pool_) {
+      if (!b.busy)
+        al.release(b.d, (size_t)b.n * 8);
+      else
+        keep.push_back(b);
+    }
+    pool_.swap(keep);
     Buf b;
     b.n = n;
     b.d = (double*)al.alloc((size_t)n * 8);

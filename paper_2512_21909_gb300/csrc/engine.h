@@ -136,7 +136,8 @@ class Engine {
   // tensor-core GEMM with 2..4 integer slices (FP64-class accuracy); applied
   // to every contraction of at least `tc_min_flops` flops (smaller ones stay
   // FP64).
-  void set_precision(int slices) { tc_slices_ = slices; }
+  // (a change drops the cached slices of the previous arithmetic)
+  void set_precision(int slices);
   int precision() const { return tc_slices_; }
   int64_t tc_min_flops = (int64_t)1 << 26;
   unsigned int* d_err = nullptr;   // device error flag of bounded waits

@@ -23,6 +23,20 @@ __device__ __forceinline__ void box_offsets(const PermTask& t, int64_t e,
                                             int* l) {
   y = t.ybase;
   x = t.xbase;
+  if (t.n <= 0x7fffffffLL) {
+    // 32-bit index arithmetic (every box below 2^31 elements)
+    int r = (int)e;
+    for (int q = t.rank - 1; q >= 0; --q) {
+      const int d = t.dim[q];
+      const int nq = r / d;
+      const int lq = r - nq * d;
+      r = nq;
+      l[q] = lq;
+      y += (int64_t)lq * t.ys[q];
+      x += (int64_t)lq * t.xs[q];
+    }
+    return;
+  }
   for (int q = t.rank - 1; q >= 0; --q) {
     const int d = t.dim[q];
     const int64_t lq = e % d;
@@ -277,6 +291,47 @@ int batched_dot(const double* G, const double* dL, int nx, int64_t nnz,
   }
   finish_dot_kernel<<<nx, 256, 0, st>>>(partial, blocks, nx, d_g);
   return launches + 1;
+}
+
+
+// ------------------------------------------------- ladder batch permutation
+namespace {
+
+template <bool INV>
+__global__ void __launch_bounds__(256)
+    ladder_perm_kernel(const __grid_constant__ LadPerm P,
+                       const double* __restrict__ src,
+                       double* __restrict__ dst) {
+  const int r = blockIdx.x;
+  int gc = 0;
+  while (gc + 1 < P.h && r >= P.row0[gc + 1]) ++gc;
+  const int loc = r - P.row0[gc];
+  const int nc = P.nc[gc], nd = P.nd[gc];
+  const int a = loc / nc, c = loc - a * nc;
+  const int len = P.nb * nd;
+  const int64_t xrow = P.xoff[gc] + (int64_t)loc * len;
+  const int64_t wbase = (int64_t)a * P.nb * P.ncol + P.coff[gc] +
+                        (int64_t)c * nd;
+  for (int e = threadIdx.x; e < len; e += blockDim.x) {
+    const int b = e / nd, d = e - b * nd;
+    const int64_t w = wbase + (int64_t)b * P.ncol + d;
+    if (INV)
+      dst[xrow + e] = src[w];
+    else
+      dst[w] = src[xrow + e];
+  }
+}
+
+}  // namespace
+
+int ladder_permute(const LadPerm& P, bool inverse, const double* src,
+                   double* dst, int rows, cudaStream_t st) {
+  if (rows <= 0) return 0;
+  if (inverse)
+    ladder_perm_kernel<true><<<rows, 256, 0, st>>>(P, src, dst);
+  else
+    ladder_perm_kernel<false><<<rows, 256, 0, st>>>(P, src, dst);
+  return 1;
 }
 
 }  // namespace cdcc

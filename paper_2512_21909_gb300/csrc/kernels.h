@@ -108,4 +108,17 @@ int batched_dot(const double* G, const double* dL, int nx, int64_t nnz,
 
 int chunk_elems();
 
+// Row-batch permutation of the on-the-fly ladder (ladder.cu):
+// X_gc[a][c][b][d] (blocks back to back at xoff[gc]) <-> W[(a,b)][coff[gc] +
+// c*nd + d] with row length ncol.  `rows` = sum over gc of na*nc.
+struct LadPerm {
+  int na, nb, h;
+  int nc[MAXIRR], nd[MAXIRR];
+  int row0[MAXIRR + 1];
+  int64_t xoff[MAXIRR], coff[MAXIRR];
+  int64_t ncol;
+};
+int ladder_permute(const LadPerm& P, bool inverse, const double* src,
+                   double* dst, int rows, cudaStream_t st);
+
 }  // namespace cdcc

@@ -100,85 +100,38 @@ void Engine::ladder_reserve(int64_t n) {
 
 // X_gc blocks of one batch: [a][c][b][d] for gc = 0..h-1, back to back.
 // forward: lad_x_ -> W rows [(a,b)][(c,d)] (leading dimension N_vv(G));
-// inverse: the same boxes read from W and written to X.
+// inverse: the same elements read from W and written to X.
+// One CTA per (a,c) row of an X_gc block: it reads (or writes) that row
+// contiguously and writes (reads) nb contiguous segments of nd elements,
+// one per W row (a,b).
 void Engine::ladder_perm(const LadBatch& b, bool inverse, const double* src,
                          double* dst) {
-  const int h = dims_.h, G = b.G;
-  // column offsets of the (c,d) sub-blocks of irrep pair G (same order as
-  // the column group of a {SO,SO,SV,SV} / {SV,SV,SV,SV} layout)
-  int64_t ncol = 0;
-  std::vector<int64_t> coff(h);
+  const int h = dims_.h, G = b.G, gb = b.ga ^ G;
+  LadPerm P;
+  std::memset(&P, 0, sizeof(P));
+  P.na = b.a1 - b.a0;
+  P.nb = dims_.n[SV][gb];
+  int64_t ncol = 0, xoff = 0;
+  int rows = 0;
   for (int gc = 0; gc < h; ++gc) {
-    coff[gc] = ncol;
-    ncol += (int64_t)dims_.n[SV][gc] * dims_.n[SV][gc ^ G];
+    const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gc ^ G];
+    P.coff[gc] = ncol;
+    P.xoff[gc] = xoff;
+    P.nc[gc] = nc;
+    P.nd[gc] = nd;
+    P.row0[gc] = rows;
+    rows += P.na * nc * (nd > 0 && P.nb > 0 ? 1 : 0);
+    ncol += (int64_t)nc * nd;
+    xoff += (int64_t)P.na * nc * P.nb * nd;
   }
-  std::ostringstream key;
-  key << "ladder:" << b.G << ':' << b.ga << ':' << b.a0 << ':' << b.a1
-      << (inverse ? 'i' : 'f');
-  auto it = task_cache_.find(key.str());
-  if (it == task_cache_.end()) {
-    const int ga = b.ga, gb = ga ^ G;
-    const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
-    std::vector<PermTask> tasks;
-    int64_t xoff = 0;
-    for (int gc = 0; gc < h; ++gc) {
-      const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gc ^ G];
-      const int64_t xsz = (int64_t)na * nc * nb * nd;
-      if (xsz > 0) {
-        PermTask t;
-        std::memset(&t, 0, sizeof(t));
-        t.rank = 4;
-        // box index order (a, b, c, d); W side and X side offsets
-        const int64_t wbase = coff[gc];
-        const int64_t ws[4] = {(int64_t)nb * ncol, ncol, nd, 1};
-        const int64_t xs[4] = {(int64_t)nc * nb * nd, nd, (int64_t)nb * nd, 1};
-        t.dim[0] = na;
-        t.dim[1] = nb;
-        t.dim[2] = nc;
-        t.dim[3] = nd;
-        for (int q = 0; q < 4; ++q) {
-          t.ys[q] = inverse ? xs[q] : ws[q];
-          t.xs[q] = inverse ? ws[q] : xs[q];
-        }
-        t.ybase = inverse ? xoff : wbase;
-        t.xbase = inverse ? wbase : xoff;
-        t.n = xsz;
-        // both boxes inside the batch buffers (last W element touched:
-        // row na*nb - 1, column coff + nc*nd - 1)
-        const int64_t wend = (int64_t)(na * nb - 1) * ncol + wbase +
-                             (int64_t)nc * nd;
-        if (xoff + xsz > b.rows * ncol || wend > b.rows * ncol ||
-            b.rows * ncol > lad_n_)
-          throw EngineError("internal: ladder permutation out of bounds");
-        tasks.push_back(t);
-      }
-      xoff += xsz;
-    }
-    if (xoff != b.rows * ncol)
-      throw EngineError("internal: ladder batch size mismatch");
-    std::vector<Chunk> chunks;
-    const int CH = chunk_elems();
-    for (int i = 0; i < (int)tasks.size(); ++i)
-      for (int64_t s = 0; s < tasks[i].n; s += CH) chunks.push_back({i, s});
-    DevTasks dt;
-    dt.ntask = (int)tasks.size();
-    dt.nchunk = (int)chunks.size();
-    if (dt.ntask) {
-      dt.tasks = (PermTask*)al.alloc(tasks.size() * sizeof(PermTask));
-      dt.chunks = (Chunk*)al.alloc(chunks.size() * sizeof(Chunk));
-      LCK(cudaMemcpyAsync(dt.tasks, tasks.data(),
-                          tasks.size() * sizeof(PermTask),
-                          cudaMemcpyHostToDevice, st_));
-      LCK(cudaMemcpyAsync(dt.chunks, chunks.data(),
-                          chunks.size() * sizeof(Chunk),
-                          cudaMemcpyHostToDevice, st_));
-      LCK(cudaStreamSynchronize(st_));
-    }
-    it = task_cache_.emplace(key.str(), dt).first;
-  }
-  const DevTasks& dt = it->second;
+  P.row0[h] = rows;
+  P.h = h;
+  P.ncol = ncol;
+  if (xoff != b.rows * ncol || b.rows * ncol > lad_n_)
+    throw EngineError("internal: ladder batch size mismatch");
+  if (rows == 0) return;
   timed(K_PERM, 16.0 * (double)b.rows * ncol, [&] {
-    return perm_axpy(dt.tasks, dt.chunks, dt.nchunk, 1.0, src, 0.0, dst, st_);
+    return ladder_permute(P, inverse, src, dst, rows, st_);
   });
 }
 
@@ -283,6 +236,7 @@ void Engine::ladder(double alpha, Tensor* T, Tensor* L, Tensor* R) {
     fl += ladder_build(b, L);
     ladder_apply_batch(b, alpha, T, R);
     fl += 2.0 * (double)b.rows * T->lay.ncol[b.G] * T->lay.nrow[b.G];
+    release_scratch();   // stream order: the next batch may reuse it
   }
   if (tr_a) {
     cudaEvent_t tr_b = get_event();
@@ -310,6 +264,7 @@ void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
   const int h = dims_.h;
   const Layout& LL = L->lay;
   for (const LadBatch& b : bs) {
+    release_scratch();   // stream order: the previous batch is queued
     fl += ladder_build(b, L);
     const double fapply =
         2.0 * (double)b.rows * T->lay.ncol[b.G] * T->lay.nrow[b.G];

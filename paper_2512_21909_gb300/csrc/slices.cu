@@ -5,7 +5,7 @@
 // Source element (row, k) = trans ? src[k*ld + row] : src[row*ld + k].
 //   float slices : x = x0 + x1 + ..., x_i = bf16(residual)      (tc_gemm.cu)
 //   exact slices : x = 2^e * sum_i X_i 2^(-8-7i), X_0 in [-256,256],
-//                  X_i in [-64,64] integers, e from the row maximum
+//                  X_i in [-64,63] integers, e from the row maximum
 //                  (tc_ozaki.cu)
 // Non-transposed sources: one CTA covers 2048 k of one row, 8 per thread,
 // one 16-byte store per slice.  Transposed sources: 64 (k) x 32 (rows)
@@ -29,28 +29,61 @@ struct Pack8 {
   __nv_bfloat16 v[8];
 };
 
+// Slices of 8 consecutive k of one row, written as one 16-byte store per
+// slice.  The arithmetic stays off the FP64 pipe (one FP64 multiply or
+// conversion per element):
+//   float: x -> FP32 (24 bits, all that three BF16 slices can hold), then
+//          x_i = bf16(r), r -= x_i in FP32 (exact)
+//   exact: q = round(x * 2^(8 - e + 7(s-1))) as a 64-bit integer (the scale
+//          is a power of two, so the product is exact), then balanced base-128
+//          digits X_{s-1}..X_1 in [-64, 63] and the leading X_0 = the rest,
+//          |X_0| <= 256; sum_i X_i 2^(-7i) = q 2^(-7(s-1)), i.e. x rounded
+//          to 8 + 7(s-1) bits below the row maximum
 template <bool EXACT>
 __device__ __forceinline__ void slice8(const double (&x)[8], int e, int s,
                                        __nv_bfloat16* dst, int64_t stride) {
-  double y[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) y[q] = EXACT ? ldexp(x[q], 8 - e) : x[q];
-  for (int i = 0; i < s; ++i) {
-    Pack8 p;
+  if (EXACT) {
+    const double scale = ldexp(1.0, 8 - e + 7 * (s - 1));
+    int dig[4][8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      if (EXACT) {
-        const double r = rint(y[q]);
-        p.v[q] = __float2bfloat16_rn((float)r);
-        y[q] = (y[q] - r) * 128.0;
-      } else {
-        const __nv_bfloat16 b = __float2bfloat16_rn((float)y[q]);
-        p.v[q] = b;
-        y[q] -= (double)__bfloat162float(b);
+      long long v = __double2ll_rn(x[q] * scale);
+#pragma unroll
+      for (int i = 3; i >= 1; --i) {
+        if (i < s) {
+          const int d = (int)((v + 64) & 127) - 64;
+          dig[i][q] = d;
+          v = (v - d) >> 7;
+        }
+      }
+      dig[0][q] = (int)v;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i < s) {
+        Pack8 p;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          p.v[q] = __float2bfloat16_rn((float)dig[i][q]);
+        *reinterpret_cast<uint4*>(dst + (int64_t)i * stride) =
+            *reinterpret_cast<const uint4*>(&p);
       }
     }
-    *reinterpret_cast<uint4*>(dst + (int64_t)i * stride) =
-        *reinterpret_cast<const uint4*>(&p);
+  } else {
+    float r[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) r[q] = __double2float_rn(x[q]);
+    for (int i = 0; i < s; ++i) {
+      Pack8 p;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(r[q]);
+        p.v[q] = b;
+        r[q] -= __bfloat162float(b);
+      }
+      *reinterpret_cast<uint4*>(dst + (int64_t)i * stride) =
+          *reinterpret_cast<const uint4*>(&p);
+    }
   }
 }
 
@@ -108,11 +141,14 @@ __global__ void rowexp_rows_kernel(const double* __restrict__ src, int rows,
   const int w = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (w >= rows) return;
-  double m = 0.0;
+  // |x| compared as bit patterns (monotone for non-negative doubles)
+  long long mb = 0;
   const double* s0 = src + (int64_t)w * ld;
-  for (int k = lane; k < K; k += 32) m = fmax(m, fabs(s0[k]));
+  for (int k = lane; k < K; k += 32)
+    mb = max(mb, __double_as_longlong(s0[k]) & 0x7fffffffffffffffLL);
   for (int o = 16; o > 0; o >>= 1)
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  const double m = __longlong_as_double(mb);
   if (lane == 0) e[w] = (m > 0.0) ? ilogb(m) + 1 : -100000;
 }
 
@@ -123,8 +159,11 @@ __global__ void rowexp_trans_kernel(const double* __restrict__ src, int rows,
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
   if (r >= rows) return;
-  double m = 0.0;
-  for (int k = k0; k < k1; ++k) m = fmax(m, fabs(src[(int64_t)k * ld + r]));
+  long long mb = 0;
+  for (int k = k0; k < k1; ++k)
+    mb = max(mb, __double_as_longlong(src[(int64_t)k * ld + r]) &
+                     0x7fffffffffffffffLL);
+  const double m = __longlong_as_double(mb);
   if (m > 0.0) atomicMax(e + r, ilogb(m) + 1);
 }
 

@@ -103,7 +103,9 @@ def footprint(req: Request, precision: int, ladder: int,
         k = {cdcc.PREC_TC: 4.5, cdcc.PREC_MIXED: 3.5}.get(precision, 2.0)
         lad = int(8 * w * k)
     else:
-        lad = int(3 * batch_gb * 1e9)
+        # two batch buffers, the batch slices and, in the density sweep, the
+        # slices of the adjoint batch (measured peaks: <= 5 batches)
+        lad = int(5.5 * batch_gb * 1e9)
     return dict(t2=t2, w=w, ovvv=ovvv, nnz=nnz, bytes=base + lad)
 
 
