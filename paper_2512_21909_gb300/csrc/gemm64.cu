@@ -9,7 +9,12 @@
 // tile), and thin products are split along K so that about four CTAs per SM
 // are available; split-K partials are summed in a fixed order (deterministic).
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "kernels.h"
 
@@ -193,8 +198,11 @@ struct Plan {
   int64_t scratch;
 };
 
-// Tile shape from the largest block; split K until ~4 CTAs per SM exist.
-Plan make_plan(const GemmProb* p, int np) {
+// Split-K factors come from a fixed reference tiling (64 x 64) so that the
+// summation order, and with it every result, does not depend on the tile
+// shape; the tile shape is the heuristic one (from the largest block) unless
+// the autotuner below picked another for this list of block shapes.
+Plan make_plan(const GemmProb* p, int np, int shape = -1) {
   Plan pl;
   std::memset(&pl, 0, sizeof(pl));
   int maxM = 0, maxN = 0;
@@ -203,21 +211,22 @@ Plan make_plan(const GemmProb* p, int np) {
       maxM = std::max(maxM, p[i].M);
       maxN = std::max(maxN, p[i].N);
     }
-  pl.bm = maxM <= 40 ? 32 : 64;
-  pl.bn = maxN <= 40 ? 32 : 64;
-  int64_t tiles = 0;
+  if (shape < 0) shape = (maxM <= 40 ? 0 : 2) + (maxN <= 40 ? 0 : 1);
+  pl.bm = (shape & 2) ? 64 : 32;
+  pl.bn = (shape & 1) ? 64 : 32;
+  int64_t ref_tiles = 0;
   for (int i = 0; i < np; ++i) {
     if (p[i].M <= 0 || p[i].N <= 0) continue;
     pl.tm[i] = (p[i].M + pl.bm - 1) / pl.bm;
     pl.tn[i] = (p[i].N + pl.bn - 1) / pl.bn;
-    tiles += (int64_t)pl.tm[i] * pl.tn[i];
+    ref_tiles += (int64_t)((p[i].M + 63) / 64) * ((p[i].N + 63) / 64);
   }
   const int64_t want = 4 * SMS;
   for (int i = 0; i < np; ++i) {
     pl.ks[i] = 1;
     if (p[i].M <= 0 || p[i].N <= 0) continue;
-    if (tiles < want && p[i].K >= 256) {
-      int ks = (int)((want + tiles - 1) / std::max<int64_t>(tiles, 1));
+    if (ref_tiles < want && p[i].K >= 256) {
+      int ks = (int)((want + ref_tiles - 1) / std::max<int64_t>(ref_tiles, 1));
       ks = std::min(ks, std::max(1, p[i].K / 128));
       ks = std::min(ks, 64);
       pl.ks[i] = std::max(1, ks);
@@ -393,10 +402,98 @@ int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
 
 namespace {
 
+// ---------------------------------------------------------------- tuner
+// The first time a list of block shapes is seen, every tile shape is timed
+// on it (outputs to a temporary buffer, CUDA events on the caller's stream)
+// and the fastest is kept for the process.  Lists whose outputs exceed 2^26
+// doubles keep the heuristic shape.  CDCC_AUTOTUNE=0 turns tuning off.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+
+bool tune_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("CDCC_AUTOTUNE");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+std::string tune_key(const GemmProb* p, int np) {
+  std::string k;
+  for (int i = 0; i < np; ++i) {
+    char b[96];
+    std::snprintf(b, sizeof(b), "%d,%d,%d,%d%d;", p[i].M, p[i].N, p[i].K,
+                  p[i].ta, p[i].tb);
+    k += b;
+  }
+  return k;
+}
+
+int launch_plan(const GemmProb* p, int np, const Plan& pl, double alpha,
+                double beta, double* scratch, cudaStream_t st);
+
+int tuned_shape(const GemmProb* p, int np, double* scratch, cudaStream_t st) {
+  if (!tune_enabled()) return -1;
+  const std::string key = tune_key(p, np);
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  int64_t out = 0;
+  for (int i = 0; i < np; ++i) out += (int64_t)p[i].M * p[i].N;
+  int best = -1;
+  if (out > 0 && out <= ((int64_t)1 << 26)) {
+    double* tmp = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaMallocAsync(&tmp, (size_t)out * 8, st) == cudaSuccess &&
+        cudaEventCreate(&a) == cudaSuccess &&
+        cudaEventCreate(&b) == cudaSuccess) {
+      GemmProb q[GEMM_MAXPROB];
+      int64_t off = 0;
+      for (int i = 0; i < np; ++i) {
+        q[i] = p[i];
+        q[i].C = tmp + off;
+        q[i].ldc = p[i].N;
+        off += (int64_t)p[i].M * p[i].N;
+      }
+      float best_ms = 0;
+      for (int shape = 0; shape < 4; ++shape) {
+        const Plan pl = make_plan(q, np, shape);
+        float ms = 0;
+        for (int rep = 0; rep < 2; ++rep) {       // second run is timed
+          cudaEventRecord(a, st);
+          launch_plan(q, np, pl, 1.0, 0.0, scratch, st);
+          cudaEventRecord(b, st);
+        }
+        if (cudaEventSynchronize(b) != cudaSuccess) break;
+        cudaEventElapsedTime(&ms, a, b);
+        if (best < 0 || ms < best_ms) {
+          best = shape;
+          best_ms = ms;
+        }
+      }
+    }
+    (void)cudaGetLastError();
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
 int grouped_tiles(const GemmProb* p, int np, double alpha, double beta,
                   double* scratch, cudaStream_t st) {
   if (np <= 0) return 0;
-  const Plan pl = make_plan(p, np);
+  const Plan pl = make_plan(p, np, tuned_shape(p, np, scratch, st));
+  return launch_plan(p, np, pl, alpha, beta, scratch, st);
+}
+
+int launch_plan(const GemmProb* p, int np, const Plan& pl, double alpha,
+                double beta, double* scratch, cudaStream_t st) {
+  if (np <= 0) return 0;
   GemmLaunch L;
   std::memset(&L, 0, sizeof(L));
   ReduceLaunch R;

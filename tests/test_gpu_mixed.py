@@ -143,3 +143,20 @@ def test_tensor_core_finish_meets_target(cd, which):
     e, g, info = _mixed(cd, s, dL, prec=cd.PREC_TC)
     assert abs(e - e_ref) <= 1e-8, abs(e - e_ref)
     assert np.abs(g - g_ref).max() <= 1e-6
+
+
+def test_fp64_gemm_tuned_shape_is_deterministic(cd):
+    """The first call of a block shape times every tile shape; the choice
+    must not change any bit of the result (split-K from a fixed tiling)."""
+    torch.manual_seed(5)
+    for (M, N, K) in [(32, 2592, 2592), (45, 70, 3000), (130, 40, 900)]:
+        A = torch.randn(M, K, dtype=torch.float64, device="cuda")
+        B = torch.randn(N, K, dtype=torch.float64, device="cuda")
+        outs = []
+        for _ in range(3):
+            C = torch.zeros(M, N, dtype=torch.float64, device="cuda")
+            cd.cdcc_dgemm(0, 1, M, N, K, 1.0, A, K, B, K, 0.0, C, N, mode=0)
+            outs.append(C.cpu())
+        assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+        ref = (A.cpu() @ B.cpu().T)
+        assert (outs[0] - ref).abs().max().item() < 1e-10 * K ** 0.5
