@@ -30,24 +30,49 @@ struct Pack8 {
 };
 
 // Slices of 8 consecutive k of one row, written as one 16-byte store per
-// slice.  The arithmetic stays off the FP64 pipe (one FP64 multiply or
-// conversion per element):
+// slice.  The arithmetic stays off the FP64 pipe (at most one conversion per
+// element):
 //   float: x -> FP32 (24 bits, all that three BF16 slices can hold), then
 //          x_i = bf16(r), r -= x_i in FP32 (exact)
-//   exact: q = round(x * 2^(8 - e + 7(s-1))) as a 64-bit integer (the scale
-//          is a power of two, so the product is exact), then balanced base-128
+//   exact: q = round(x * 2^(8 - e + 7(s-1))) as a 64-bit integer, taken
+//          from the bit pattern of x with integer operations, then balanced base-128
 //          digits X_{s-1}..X_1 in [-64, 63] and the leading X_0 = the rest,
 //          |X_0| <= 256; sum_i X_i 2^(-7i) = q 2^(-7(s-1)), i.e. x rounded
 //          to 8 + 7(s-1) bits below the row maximum
+// round(x * 2^sh) to the nearest integer, ties to even (the rounding of
+// __double2ll_rn), from the bit pattern with integer operations only.
+// Valid while |x * 2^sh| < 2^62; zero and subnormal x give 0.
+__device__ __forceinline__ long long round_scaled(double x, int sh) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0) return 0;
+  const long long mant = (b & 0xfffffffffffffLL) | (1LL << 52);
+  const int shift = E - 1075 + sh;          // |x| 2^sh = mant 2^shift
+  long long q;
+  if (shift >= 0) {
+    q = mant << min(shift, 9);
+  } else if (shift < -63) {
+    q = 0;
+  } else {
+    const int r = -shift;
+    q = mant >> r;
+    const unsigned long long rem =
+        (unsigned long long)mant & ((1ULL << r) - 1ULL);
+    const unsigned long long half = 1ULL << (r - 1);
+    if (rem > half || (rem == half && (q & 1))) ++q;
+  }
+  return b < 0 ? -q : q;
+}
+
 template <bool EXACT>
 __device__ __forceinline__ void slice8(const double (&x)[8], int e, int s,
                                        __nv_bfloat16* dst, int64_t stride) {
   if (EXACT) {
-    const double scale = ldexp(1.0, 8 - e + 7 * (s - 1));
+    const int sh = 8 - e + 7 * (s - 1);
     int dig[4][8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      long long v = __double2ll_rn(x[q] * scale);
+      long long v = round_scaled(x[q], sh);
 #pragma unroll
       for (int i = 3; i >= 1; --i) {
         if (i < s) {
