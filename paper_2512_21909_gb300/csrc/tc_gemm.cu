@@ -258,15 +258,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   __syncwarp();
 
-  // ---- epilogue: 4 warps x 32 TMEM lanes = 128 rows
+  // ---- epilogue: 4 warps x 32 TMEM lanes = 128 rows of the 128-row side.
+  // With the logical rows there (trans_out = 0) a lane holds one row of C;
+  // each warp then passes 32 x 16 sub-tiles through shared memory (the
+  // stage buffers are free once every MMA has completed) so that
+  // consecutive lanes write consecutive columns.
   bool have = nit > 0;
   if (have) have = mbar_wait(done, 0, L.err, 3);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int r = m0 + warp * 32 + lane;  // row of the 128-row side
   const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
   const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
   double* C = L.C[pi];
   const int ldc = L.ldc[pi];
+  auto put = [&](int m, int n, double dv) {   // logical C element (m, n)
+    if (ksn == 1) {
+      double* p = C + (int64_t)m * ldc + n;
+      const double val = L.alpha * dv;
+      *p = (L.beta == 0.0) ? val : fma(L.beta, *p, val);
+    } else {
+      L.scratch[L.poff[pi] + (int64_t)ksi * L.M[pi] * L.N[pi] +
+                (int64_t)m * L.N[pi] + n] = dv;
+    }
+  };
+  double* stg = reinterpret_cast<double*>(smem) + warp * (32 * 17);
   float v[32];
   for (int c0 = 0; c0 < BN; c0 += 32) {
     if (have) {
@@ -275,20 +289,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int i = 0; i < 32; ++i) v[i] = 0.f;
     }
-    if (r >= Mr) continue;
+    if (L.trans_out) {
+      // lanes run along n already
+      const int r = m0 + warp * 32 + lane;
+      if (r < Mr) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      const int cc = n0 + c0 + i;
-      if (cc >= Nc) break;
-      // logical C element (m, n)
-      const int m = L.trans_out ? cc : r, n = L.trans_out ? r : cc;
-      if (ksn == 1) {
-        double* p = C + (int64_t)m * ldc + n;
-        const double val = L.alpha * (double)v[i];
-        *p = (L.beta == 0.0) ? val : fma(L.beta, *p, val);
-      } else {
-        L.scratch[L.poff[pi] + (int64_t)ksi * L.M[pi] * L.N[pi] +
-                  (int64_t)m * L.N[pi] + n] = (double)v[i];
+        for (int i = 0; i < 32; ++i) {
+          const int cc = n0 + c0 + i;
+          if (cc >= Nc) break;
+          put(cc, r, (double)v[i]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < 32; h += 16) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = (double)v[h + j];
+        __syncwarp();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; rr += 2) {
+          const int row = rr + (lane >> 4), col = lane & 15;
+          const int m = m0 + warp * 32 + row, n = n0 + c0 + h + col;
+          if (m < Mr && n < Nc) put(m, n, stg[row * 17 + col]);
+        }
       }
     }
   }

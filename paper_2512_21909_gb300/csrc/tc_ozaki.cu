@@ -18,8 +18,10 @@
 //     chunk n overlaps the MMAs of chunk n+1.
 // Operands are staged by TMA (128B swizzle) through a 2-stage pipeline; one
 // thread issues tcgen05.mma.kind::f16.  Tile: 128 rows x 64 columns (the
-// larger output dimension on the 128-row side).  Every mbarrier wait is
-// bounded and sets the error flag on timeout.
+// larger output dimension on the 128-row side); the kernel is persistent
+// (one CTA per SM walks its tiles), so one tile's drain and write overlap
+// the next tile's loads and MMAs.  Every mbarrier wait is bounded and sets
+// the error flag on timeout.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -166,6 +168,20 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   lo += e;
 }
 
+// Tile t of the launch -> (problem, 128-row tile, 64-column tile).
+__device__ __forceinline__ void oz_tile(const OzLaunch& L, int t, int& pi,
+                                        int& m0, int& n0) {
+  pi = 0;
+  while (pi + 1 < L.np && t >= L.tile0[pi + 1]) ++pi;
+  const int local = t - L.tile0[pi];
+  m0 = (local / L.tn[pi]) * OZ_BM;
+  n0 = (local % L.tn[pi]) * OZ_BN;
+}
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ...  The three roles walk
+// the same tile sequence with running counters (K blocks for the smem
+// stages, K chunks for the two accumulator sets), so the loads and MMAs of
+// the next tile proceed while the drain warps finish and write this one.
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ OzLaunch L) {
   extern __shared__ uint8_t smem_raw[];
@@ -177,16 +193,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint64_t* empty = full + OZ_STAGES;
   uint64_t* accf = empty + OZ_STAGES;   // [2] accumulator set ready
   uint64_t* acce = accf + 2;            // [2] accumulator set drained
-  uint32_t* tmem_slot = (uint32_t*)(acce + 2);
+  uint64_t* fin = acce + 2;             // all MMAs of this CTA complete
+  uint32_t* tmem_slot = (uint32_t*)(fin + 1);
+  int* consumed = (int*)(tmem_slot + 1);   // K blocks the MMA side used
+  // per drain warp a 32 x 16 staging tile for coalesced writes of C
+  double* stage_out =
+      (double*)(smem + (size_t)OZ_STAGES * stage_bytes + 256);
 
-  const int bid = blockIdx.x;
-  int pi = 0;
-  while (pi + 1 < L.np && bid >= L.tile0[pi + 1]) ++pi;
-  const int local = bid - L.tile0[pi];
-  const int tn = local % L.tn[pi], tm = local / L.tn[pi];
-  const int m0 = tm * OZ_BM, n0 = tn * OZ_BN;
-  const int nkb = L.nkb[pi];
-  const int nch = (nkb + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
+  const int ntile = L.tile0[L.np];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t NCOLS = 512;   // two sets of s (<= 4) x 64 columns
 
@@ -199,6 +213,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       bar_init(&accf[i], 1);
       bar_init(&acce[i], 4);   // one arrive per drain warp
     }
+    bar_init(fin, 1);
+    *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -217,22 +233,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                          ((uint32_t)(OZ_BN >> 3) << 17) |
                          ((uint32_t)(OZ_BM >> 4) << 24);
+  int issued = 0;   // producer: K blocks whose loads were issued
 
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer
-      for (int it = 0; it < nkb; ++it) {
-        const int st = it % OZ_STAGES, round = it / OZ_STAGES;
-        if (round > 0 && !bar_wait(&empty[st], (round - 1) & 1, L.err, 11))
-          break;
-        bar_expect(&full[st], stage_bytes);
-        uint8_t* sa = smem + (size_t)st * stage_bytes;
-        uint8_t* sb = sa + (size_t)s * A_BYTES;
-        for (int i = 0; i < s; ++i) {
-          tma3(sa + (size_t)i * A_BYTES, &L.ta[pi], it * OZ_BK, m0, i,
-               &full[st]);
-          tma3(sb + (size_t)i * B_BYTES, &L.tb[pi], it * OZ_BK, n0, i,
-               &full[st]);
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+        int pi, m0, n0;
+        oz_tile(L, t, pi, m0, n0);
+        for (int kb = 0; kb < L.nkb[pi]; ++kb, ++g) {
+          const int st = g % OZ_STAGES, round = g / OZ_STAGES;
+          if (round > 0 && !bar_wait(&empty[st], (round - 1) & 1, L.err, 11)) {
+            ok = false;
+            break;
+          }
+          bar_expect(&full[st], stage_bytes);
+          uint8_t* sa = smem + (size_t)st * stage_bytes;
+          uint8_t* sb = sa + (size_t)s * A_BYTES;
+          for (int i = 0; i < s; ++i) {
+            tma3(sa + (size_t)i * A_BYTES, &L.ta[pi], kb * OZ_BK, m0, i,
+                 &full[st]);
+            tma3(sb + (size_t)i * B_BYTES, &L.tb[pi], kb * OZ_BK, n0, i,
+                 &full[st]);
+          }
+          issued = g + 1;
         }
       }
     }
@@ -240,95 +266,152 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (lane == 0) {
       // ---- MMA issuer: chunk c -> accumulator set c & 1
       bool ok = true;
-      for (int c = 0; c < nch && ok; ++c) {
-        const int set = c & 1;
-        if (c >= 2 && !bar_wait(&acce[set], ((c >> 1) - 1) & 1, L.err, 12)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int kb0 = c * OZ_KBLK_PER_CHUNK;
-        const int kb1 = min(nkb, kb0 + OZ_KBLK_PER_CHUNK);
-        for (int kb = kb0; kb < kb1; ++kb) {
-          const int st = kb % OZ_STAGES, round = kb / OZ_STAGES;
-          if (!bar_wait(&full[st], round & 1, L.err, 13)) {
+      int g = 0, c = 0;
+      for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+        int pi, m0, n0;
+        oz_tile(L, t, pi, m0, n0);
+        const int nkb = L.nkb[pi];
+        const int nch = (nkb + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
+        for (int ch = 0; ch < nch && ok; ++ch, ++c) {
+          const int set = c & 1;
+          if (c >= 2 &&
+              !bar_wait(&acce[set], ((c >> 1) - 1) & 1, L.err, 12)) {
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sa = su32(smem + (size_t)st * stage_bytes);
-          const uint32_t sb = sa + (uint32_t)s * A_BYTES;
-          for (int d = 0; d < s; ++d) {
-            const uint32_t acc_addr = tmem + (uint32_t)((set * s + d) * OZ_BN);
-            int first = (kb == kb0);
-            for (int i = 0; i <= d; ++i) {
-              const int j = d - i;
+          const int kb0 = ch * OZ_KBLK_PER_CHUNK;
+          const int kb1 = min(nkb, kb0 + OZ_KBLK_PER_CHUNK);
+          for (int kb = kb0; kb < kb1; ++kb, ++g) {
+            const int st = g % OZ_STAGES, round = g / OZ_STAGES;
+            if (!bar_wait(&full[st], round & 1, L.err, 13)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = su32(smem + (size_t)st * stage_bytes);
+            const uint32_t sb = sa + (uint32_t)s * A_BYTES;
+            for (int d = 0; d < s; ++d) {
+              const uint32_t acc_addr =
+                  tmem + (uint32_t)((set * s + d) * OZ_BN);
+              int first = (kb == kb0);
+              for (int i = 0; i <= d; ++i) {
+                const int j = d - i;
 #pragma unroll
-              for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-                umma(acc_addr, sdesc(sa + i * A_BYTES + kk * 32),
-                     sdesc(sb + j * B_BYTES + kk * 32), idesc,
-                     first ? 0u : 1u);
-                first = 0;
+                for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+                  umma(acc_addr, sdesc(sa + i * A_BYTES + kk * 32),
+                       sdesc(sb + j * B_BYTES + kk * 32), idesc,
+                       first ? 0u : 1u);
+                  first = 0;
+                }
               }
             }
+            ucommit(&empty[st]);
+            *(volatile int*)consumed = g + 1;
           }
-          ucommit(&empty[st]);
+          if (!ok) break;
+          ucommit(&accf[set]);
         }
-        ucommit(&accf[set]);
       }
+      ucommit(fin);   // arrives once every MMA issued above has completed
     }
   } else {
     // ---- drain warps 2..5: TMEM sub-partition (warp % 4), 32 rows each
     const int sub = warp & 3;
-    float hi[OZ_BN], lo[OZ_BN];
+    bool ok = true;
+    int c = 0;
+    for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+      int pi, m0, n0;
+      oz_tile(L, t, pi, m0, n0);
+      const int nch = (L.nkb[pi] + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
+      float hi[OZ_BN], lo[OZ_BN];
 #pragma unroll
-    for (int i = 0; i < OZ_BN; ++i) hi[i] = lo[i] = 0.f;
-    for (int c = 0; c < nch; ++c) {
-      const int set = c & 1;
-      if (!bar_wait(&accf[set], (c >> 1) & 1, L.err, 14)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int d = 0; d < s; ++d) {
-        const float sc = exp2f(-16.0f - 7.0f * d);
-#pragma unroll
-        for (int c0 = 0; c0 < OZ_BN; c0 += 32) {
-          float v[32];
-          tld32(tmem + ((uint32_t)(sub * 32) << 16) +
-                    (uint32_t)((set * s + d) * OZ_BN + c0),
-                v);
-#pragma unroll
-          for (int q = 0; q < 32; ++q) two_sum_add(hi[c0 + q], lo[c0 + q],
-                                                   v[q] * sc);
+      for (int i = 0; i < OZ_BN; ++i) hi[i] = lo[i] = 0.f;
+      for (int ch = 0; ch < nch; ++ch, ++c) {
+        const int set = c & 1;
+        if (!bar_wait(&accf[set], (c >> 1) & 1, L.err, 14)) {
+          ok = false;
+          break;
         }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int d = 0; d < s; ++d) {
+          const float sc = exp2f(-16.0f - 7.0f * d);
+#pragma unroll
+          for (int c0 = 0; c0 < OZ_BN; c0 += 32) {
+            float v[32];
+            tld32(tmem + ((uint32_t)(sub * 32) << 16) +
+                      (uint32_t)((set * s + d) * OZ_BN + c0),
+                  v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              two_sum_add(hi[c0 + q], lo[c0 + q], v[q] * sc);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) bar_arrive(&acce[set]);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) bar_arrive(&acce[set]);
-    }
-    // ---- write: row r of the 128-row side, 64 columns
-    const int r = m0 + sub * 32 + lane;
-    const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
-    const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
-    if (r < Mr) {
-      const int er = L.erow[pi][r];
+      if (!ok) break;
+      // ---- write: row r of the 128-row side, 64 columns.  With the
+      // logical rows on that side (trans_out = 0) the warp passes 32 x 16
+      // sub-tiles through shared memory so that lanes run along n.
+      const int r = m0 + sub * 32 + lane;
+      const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
+      const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
+      const int er = r < Mr ? L.erow[pi][r] : 0;
       double* C = L.C[pi];
       const int ldc = L.ldc[pi];
+      auto put = [&](int m, int n, double val) {
+        double* p = C + (int64_t)m * ldc + n;
+        const double out = L.alpha * val;
+        *p = (L.beta == 0.0) ? out : fma(L.beta, *p, out);
+      };
+      if (L.trans_out) {
+        if (r < Mr) {
 #pragma unroll
-      for (int q = 0; q < OZ_BN; ++q) {
-        const int cc = n0 + q;
-        if (cc < Nc) {
-          const double val =
-              ldexp((double)hi[q] + (double)lo[q], er + L.ecol[pi][cc]);
-          const int m = L.trans_out ? cc : r, n = L.trans_out ? r : cc;
-          double* p = C + (int64_t)m * ldc + n;
-          const double out = L.alpha * val;
-          *p = (L.beta == 0.0) ? out : fma(L.beta, *p, out);
+          for (int q = 0; q < OZ_BN; ++q) {
+            const int cc = n0 + q;
+            if (cc < Nc)
+              put(cc, r, ldexp((double)hi[q] + (double)lo[q],
+                               er + L.ecol[pi][cc]));
+          }
+        }
+      } else {
+        double* stg = stage_out + sub * (32 * 17);
+#pragma unroll
+        for (int h = 0; h < OZ_BN; h += 16) {
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int cc = n0 + h + j;
+            const int ec = cc < Nc ? L.ecol[pi][cc] : 0;
+            stg[lane * 17 + j] =
+                ldexp((double)hi[h + j] + (double)lo[h + j], er + ec);
+          }
+          __syncwarp();
+#pragma unroll 4
+          for (int rr = 0; rr < 32; rr += 2) {
+            const int row = rr + (lane >> 4), col = lane & 15;
+            const int m = m0 + sub * 32 + row, n = n0 + h + col;
+            if (m < Mr && n < Nc) put(m, n, stg[row * 17 + col]);
+          }
         }
       }
     }
   }
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (warp == 0 && lane == 0) {
+    // loads issued but never consumed (only after a timeout): wait for them
+    // to land before the CTA leaves (bounded)
+    for (int g = *(volatile int*)consumed; g < issued; ++g)
+      bar_wait(&full[g % OZ_STAGES], (g / OZ_STAGES) & 1, L.err, 15);
+  }
   if (warp == 1) {
+    if (lane == 0) bar_wait(fin, 0, L.err, 16);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
                      tmem),
                  "r"(NCOLS)
@@ -416,10 +499,16 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->beta = beta;
   L->err = d_err;
   const int stage = nslice * (OZ_BM * 128 + OZ_BN * 128);
-  const int smem = OZ_STAGES * stage + 1024 + 256;
+  // stages, barriers, and four 32 x 17 double staging tiles for the output
+  const int smem = OZ_STAGES * stage + 1024 + 256 + 4 * 32 * 17 * 8;
   cudaFuncSetAttribute(oz_gemm_kernel,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  oz_gemm_kernel<<<tiles, OZ_THREADS, smem, st>>>(*L);
+  // persistent: one CTA per SM (at most one fits), tiles strided over them
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(tiles, sms));
+  oz_gemm_kernel<<<grid, OZ_THREADS, smem, st>>>(*L);
   delete L;
   return 1;
 }
