@@ -29,7 +29,6 @@
 #include <stdexcept>
 #include <string>
 
-#include "fpbits.cuh"
 #include "kernels.h"
 
 namespace cdcc {
@@ -271,12 +270,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
   double* C = L.C[pi];
   const int ldc = L.ldc[pi];
-  const bool unit = L.alpha == 1.0, acc = L.beta != 0.0;
   auto put = [&](int m, int n, double dv) {   // logical C element (m, n)
     if (ksn == 1) {
       double* p = C + (int64_t)m * ldc + n;
-      const double val = unit ? dv : L.alpha * dv;
-      *p = acc ? fma(L.beta, *p, val) : val;
+      const double val = L.alpha * dv;
+      *p = (L.beta == 0.0) ? val : fma(L.beta, *p, val);
     } else {
       L.scratch[L.poff[pi] + (int64_t)ksi * L.M[pi] * L.N[pi] +
                 (int64_t)m * L.N[pi] + n] = dv;
@@ -299,7 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int i = 0; i < 32; ++i) {
           const int cc = n0 + c0 + i;
           if (cc >= Nc) break;
-          put(cc, r, f2d_pow2(v[i], 0));
+          put(cc, r, (double)v[i]);
         }
       }
     } else {
@@ -307,7 +305,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int h = 0; h < 32; h += 16) {
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = f2d_pow2(v[h + j], 0);
+        for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = (double)v[h + j];
         __syncwarp();
 #pragma unroll 4
         for (int rr = 0; rr < 32; rr += 2) {

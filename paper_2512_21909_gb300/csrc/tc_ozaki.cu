@@ -33,7 +33,6 @@
 #include <stdexcept>
 #include <string>
 
-#include "fpbits.cuh"
 #include "kernels.h"
 
 namespace cdcc {
@@ -362,11 +361,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int er = r < Mr ? L.erow[pi][r] : 0;
       double* C = L.C[pi];
       const int ldc = L.ldc[pi];
-      const bool unit = L.alpha == 1.0, acc = L.beta != 0.0;
       auto put = [&](int m, int n, double val) {
         double* p = C + (int64_t)m * ldc + n;
-        const double out = unit ? val : L.alpha * val;
-        *p = acc ? fma(L.beta, *p, out) : out;
+        const double out = L.alpha * val;
+        *p = (L.beta == 0.0) ? out : fma(L.beta, *p, out);
       };
       if (L.trans_out) {
         if (r < Mr) {
@@ -374,8 +372,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int q = 0; q < OZ_BN; ++q) {
             const int cc = n0 + q;
             if (cc < Nc)
-              put(cc, r, f2d_pow2(hi[q], er + L.ecol[pi][cc]) +
-                             f2d_pow2(lo[q], er + L.ecol[pi][cc]));
+              put(cc, r, ldexp((double)hi[q] + (double)lo[q],
+                               er + L.ecol[pi][cc]));
           }
         }
       } else {
@@ -387,10 +385,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int j = 0; j < 16; ++j) {
             const int cc = n0 + h + j;
             const int ec = cc < Nc ? L.ecol[pi][cc] : 0;
-            // 2^k (hi + lo): the exact scaling on the integer pipe, one
-            // FP64 add
             stg[lane * 17 + j] =
-                f2d_pow2(hi[h + j], er + ec) + f2d_pow2(lo[h + j], er + ec);
+                ldexp((double)hi[h + j] + (double)lo[h + j], er + ec);
           }
           __syncwarp();
 #pragma unroll 4
