@@ -130,6 +130,24 @@ def test_bounded_wait_gives_up_and_device_stays_usable(cd):
     assert np.isfinite(e) and np.all(np.isfinite(g))
 
 
+def test_raw_c0_divergence_is_reported(cd):
+    """c0 with the literal Cholesky distribution (s = 1, E_MP2 = -37 Eh) is
+    the strong-correlation stress case: the oracle's CCSD diverges on it
+    (plain Jacobi reaches NaN, DIIS turns singular).  The library must end
+    with an error status, not hang or return a number, and stay usable."""
+    s = make_system(0, scale=1.0)
+    ctx = cd.init_from_system(s)
+    with pytest.raises(cd.CdccError) as ei:
+        cd.ccsd_solve(ctx)
+    assert ei.value.status in (cd.CDCC_ENUMERIC, cd.CDCC_ENOCONV)
+    cd.cd_ccsd_free(ctx)
+    t = random_system([1], [2], [3], seed=23, scale=0.4)
+    ctx = cd.init_from_system(t)
+    e, g = cd.gradient(ctx, make_displacements(t, 1))
+    cd.cd_ccsd_free(ctx)
+    assert np.isfinite(e) and np.all(np.isfinite(g))
+
+
 def test_call_order_enforced(cd):
     s = random_system([1], [2], [3], seed=9, scale=0.4)
     ctx = cd.init_from_system(s)

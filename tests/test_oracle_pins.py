@@ -312,3 +312,13 @@ def test_rows_planted_mistake_is_caught(monkeypatch):
     _, R2 = rows.residual_rows(T(t1), T(t2), T(h), T(L), 2, [(0, 1)])
     assert calls["n"] > 0
     assert np.abs(R2[(0, 1)].numpy() - R2b[0, 1]).max() > 1e-4
+
+
+def test_raw_c0_diverges():
+    """The literal distribution (s = 1) gives E_MP2 = -37 Eh for c0 and the
+    CCSD iterations diverge (the reason for the energy scale s_cfg)."""
+    s = make_system(0, scale=1.0)
+    L, h = _sys_dense(s)
+    assert mp2.mp2_energy(s.eps, L, s.nocc) < -30.0
+    with pytest.raises(Exception):
+        ccsd.solve_ccsd(T(h), T(L), s.nocc, tol=1e-10, maxiter=60, ndiis=0)
