@@ -168,6 +168,26 @@ cdcc_status cdcc_get_gamma(cdcc_ctx *ctx, double *gamma);
 cdcc_status contract_dL(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
                         const double *dL, double *g);
 
+/*
+ * Error report of a result (the precision schedule of Sec. 2 / cdcc_options):
+ * what the schedule's reduced-precision arithmetic changed, measured against
+ * FP64 DFMA arithmetic at the same converged amplitudes t and multipliers
+ * lambda.
+ *   *dE    |E_FP64(t) - E(t)| + |<lambda, R_FP64(t)>|: the FP64 equations
+ *          leave a residual R_FP64 at the schedule's t, and to first order the
+ *          FP64 energy at its own solution differs from E_FP64(t) by
+ *          -<lambda, R_FP64>;
+ *   dg[x]  |<Gamma_FP64 - Gamma, dL_x>| with Gamma_FP64 from a density sweep
+ *          in FP64 at (t, lambda) (the effect of the amplitude and multiplier
+ *          errors on g is not included).
+ * nx, x_irrep, dL as for contract_dL (nx may be 0, then dg is not touched).
+ * Cost: one FP64 residual evaluation and one FP64 density sweep.  Gamma^P
+ * and D of the context are left as they were.  Requires build_density; with
+ * the FP64 schedule the numbers reflect the convergence threshold only.
+ */
+cdcc_status cdcc_error_estimate(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
+                                const double *dL, double *dE, double *dg);
+
 /* Everything that has not run yet, then contract_dL. */
 cdcc_status gradient(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
                      const double *dL, double *e_corr, double *g);

@@ -266,6 +266,29 @@ def contract_dL(ctx, dL, nx=None, x_irrep=None):
     return g
 
 
+def cdcc_error_estimate(ctx, dL=None, nx=None, x_irrep=None):
+    """(dE, dg[nx]): change of E and g caused by the schedule's reduced
+    precision, measured against FP64 at the converged t and lambda."""
+    lib = load()
+    lib.cdcc_error_estimate.argtypes = [ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]
+    lib.cdcc_error_estimate.restype = ctypes.c_int
+    dE = ctypes.c_double()
+    if dL is None:
+        _check(ctx, lib.cdcc_error_estimate(ctx.handle, 0, None, None,
+                                            ctypes.byref(dE), None))
+        return dE.value, np.zeros(0)
+    if nx is None:
+        nx = dL.shape[0] if getattr(dL, "ndim", 1) > 1 else 1
+    xi, xp, d, dp = _displacements(dL, x_irrep, nx)
+    dg = np.zeros(nx)
+    _check(ctx, lib.cdcc_error_estimate(
+        ctx.handle, int(nx), xp, dp, ctypes.byref(dE),
+        dg.ctypes.data_as(ctypes.c_void_p)))
+    return dE.value, dg
+
+
 def gradient(ctx, dL, nx=None, x_irrep=None):
     if nx is None:
         nx = dL.shape[0] if getattr(dL, "ndim", 1) > 1 else 1

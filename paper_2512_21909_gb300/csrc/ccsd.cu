@@ -632,6 +632,8 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
   c->state = 3;
 }
 
+void assemble_density(cdcc_ctx* c);
+
 void run_density(cdcc_ctx* c, double* D1) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 2);
@@ -640,6 +642,22 @@ void run_density(cdcc_ctx* c, double* D1) {
   e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}},
              TAG_L | TAG_H);
   e.set_precision(0);
+  assemble_density(c);
+  pt.stop();
+  if (D1) {
+    const int n = c->hd.n;
+    std::vector<double> h = to_host(c, c->D1s);
+    std::vector<double> dense((size_t)n * n, 0.0);
+    visit_dense(c->D1s->lay, c->dims,
+                [&](int64_t off, int64_t di) { dense[di] = h[off]; });
+    std::memcpy(D1, dense.data(), dense.size() * 8);
+  }
+  c->state = 4;
+}
+
+// Gamma^P and D from the adjoints left by the density sweep.
+void assemble_density(cdcc_ctx* c) {
+  Engine& e = *c->eng;
   // Gamma^P_pq: embed the block adjoints into the packed pattern, symmetrise
   e.zero(c->Gam);
   e.axpy(1.0, e.adjoint(c->Loo), "Pij", 1.0, c->Gam, "Pij");
@@ -656,16 +674,6 @@ void run_density(cdcc_ctx* c, double* D1) {
   e.axpy(1.0, e.adjoint(c->hvv), "ab", 1.0, c->D1a, "ab");
   e.axpy(0.5, c->D1a, "pq", 0.0, c->D1s, "pq");
   e.axpy(0.5, c->D1a, "qp", 1.0, c->D1s, "pq");
-  pt.stop();
-  if (D1) {
-    const int n = c->hd.n;
-    std::vector<double> h = to_host(c, c->D1s);
-    std::vector<double> dense((size_t)n * n, 0.0);
-    visit_dense(c->D1s->lay, c->dims,
-                [&](int64_t off, int64_t di) { dense[di] = h[off]; });
-    std::memcpy(D1, dense.data(), dense.size() * 8);
-  }
-  c->state = 4;
 }
 
 size_t packed_size_g(const cdcc_ctx* c, int gx) {
@@ -728,6 +736,53 @@ void run_contract(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   e.release_scratch();
   pt.stop();
   std::memcpy(g, out.data(), nx * 8);
+}
+
+// What the reduced-precision arithmetic of the schedule changed, measured
+// against FP64 DFMA arithmetic at the same converged (t, lambda):
+//   dE   = |E64(t) - E(t)| + |<lambda, R64(t)>|: the FP64 equations leave a
+//          residual R64 at the schedule's amplitudes, and to first order the
+//          FP64 energy at its own solution differs by -<lambda, R64>;
+//   dg_x = |<Gamma64 - Gamma, dL_x>| from an FP64 density sweep.
+// Gamma^P and D of the context are restored afterwards.
+void run_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
+                        const double* dL, double* dE, double* dg) {
+  Engine& e = *c->eng;
+  std::vector<double> g0(std::max(nx, 1)), g64(std::max(nx, 1));
+  if (nx > 0) run_contract(c, nx, x_irrep, dL, g0.data());
+  const int64_t ng = c->Gsym->lay.size, nd = c->D1s->lay.size;
+  Tensor* keepG = e.flat("errest_G", ng);
+  Tensor* keepD = e.flat("errest_D", nd);
+  CK(cudaMemcpyAsync(keepG->d, c->Gsym->d, (size_t)ng * 8,
+                     cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(keepD->d, c->D1s->d, (size_t)nd * 8,
+                     cudaMemcpyDeviceToDevice, c->st));
+  ensure_tape(c);
+  const int prec = e.precision();
+  e.set_precision(0);
+  residual(c);                       // FP64 E, R and tape intermediates at t
+  const double E64 = scalar(c, c->E) - c->e_ref;
+  const double* lam = c->lam->d;
+  e.timed(Engine::K_OTHER, 16.0 * c->lam->lay.size, [&] {
+    return multi_dot(&lam, 1, c->res->d, c->lam->lay.size, c->d_partial,
+                     c->d_dots, c->st);
+  });
+  double lr = 0;
+  CK(cudaMemcpyAsync(&lr, c->d_dots, 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  *dE = std::fabs(E64 - c->e_corr) + std::fabs(lr);
+  e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}},
+             TAG_L | TAG_H);
+  assemble_density(c);
+  if (nx > 0) run_contract(c, nx, x_irrep, dL, g64.data());
+  for (int x = 0; x < nx; ++x) dg[x] = std::fabs(g64[x] - g0[x]);
+  CK(cudaMemcpyAsync(c->Gsym->d, keepG->d, (size_t)ng * 8,
+                     cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemcpyAsync(c->D1s->d, keepD->d, (size_t)nd * 8,
+                     cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  e.set_precision(prec);
+  check_device_error(c);
 }
 
 void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
@@ -1084,6 +1139,17 @@ cdcc_status contract_dL(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   if (nx < 0 || (nx > 0 && (!dL || !g))) return CDCC_EINVAL;
   if (nx == 0) return CDCC_OK;
   return guarded(c, [&] { run_contract(c, nx, x_irrep, dL, g); });
+}
+
+cdcc_status cdcc_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
+                                const double* dL, double* dE, double* dg) {
+  if (!c || !dE) return CDCC_EINVAL;
+  if (c->state < 4) {
+    c->err = "cdcc_error_estimate before build_density";
+    return CDCC_ESTATE;
+  }
+  if (nx < 0 || (nx > 0 && (!dL || !dg))) return CDCC_EINVAL;
+  return guarded(c, [&] { run_error_estimate(c, nx, x_irrep, dL, dE, dg); });
 }
 
 cdcc_status gradient(cdcc_ctx* c, int nx, const int32_t* x_irrep,

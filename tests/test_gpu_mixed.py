@@ -160,3 +160,38 @@ def test_fp64_gemm_tuned_shape_is_deterministic(cd):
         assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
         ref = (A.cpu() @ B.cpu().T)
         assert (outs[0] - ref).abs().max().item() < 1e-10 * K ** 0.5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "tc"])
+def test_error_estimate_brackets_the_measured_error(cd, prec):
+    """cdcc_error_estimate against the error actually measured on c1 (the
+    same gradient with the FP64 schedule): the estimate is of the right
+    size (a first-order quantity: within a factor 10 of the measured energy
+    error above the 1e-11 convergence noise), below the 1e-8 Eh / 1e-6
+    targets, and it leaves Gamma and g unchanged."""
+    s = make_system(1)
+    dL = make_displacements(s, 4)
+    ref = cd.init_from_system(s)
+    e64, g64 = cd.gradient(ref, dL)
+    cd.cd_ccsd_free(ref)
+    o = cd.cdcc_default_options()
+    o.precision = {"fp64": cd.PREC_FP64, "mixed": cd.PREC_MIXED,
+                   "tc": cd.PREC_TC}[prec]
+    ctx = cd.init_from_system(s, options=o)
+    e, g = cd.gradient(ctx, dL)
+    G = cd.cdcc_get_gamma(ctx)
+    dE, dg = cd.cdcc_error_estimate(ctx, dL)
+    assert np.array_equal(cd.cdcc_get_gamma(ctx), G)
+    assert np.array_equal(cd.contract_dL(ctx, dL), g)
+    cd.cd_ccsd_free(ctx)
+    err = abs(e - e64)
+    assert np.isfinite(dE) and dE >= 0 and np.all(dg >= 0)
+    assert dE <= 1e-8 and np.abs(dg).max() <= 1e-6
+    if prec == "fp64":
+        assert dE < 1e-11 and np.abs(dg).max() < 1e-12
+    else:
+        # not an underestimate beyond the convergence noise, and not an
+        # overestimate by more than 10x once the error is above that noise
+        assert err <= 10 * dE + 1e-11, (err, dE)
+        if err > 1e-11:
+            assert dE <= 10 * err, (err, dE)
