@@ -49,6 +49,9 @@ def parse():
                     help="other schedules to time beside --precision: "
                          "'all', 'none' or a comma list")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--error-estimate", action="store_true",
+                    help="after the timed steps, run cdcc_error_estimate "
+                         "(one FP64 residual and density sweep, untimed)")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload (Poisson arrivals of "
                          "mixed requests) instead of a fixed workload")
@@ -296,6 +299,22 @@ def run_ours(args, rank, ws):
             "ladder_tflops": lad[1] / lad[0] / 1e12 if lad[0] > 0 else None})
     args.precision = saved
 
+    # ---- error report of the --precision schedule (untimed)
+    err_est = None
+    if args.error_estimate:
+        ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
+                                s.orb_irrep, s.eps, s.chol_irrep, L_d,
+                                options=options())
+        cdcc.gradient(ctx, dL_d)
+        t0 = time.perf_counter()
+        dE, dg = cdcc.cdcc_error_estimate(ctx, dL_d)
+        err_est = {"dE": dE, "max_dg": float(np.abs(dg).max()),
+                   "seconds": time.perf_counter() - t0,
+                   "what": "|E64(t)-E(t)| + |<lambda,R64(t)>| and "
+                           "|<Gamma64-Gamma, dL>| against FP64 at the "
+                           "converged t, lambda"}
+        cdcc.cd_ccsd_free(ctx)
+
     # ---- end to end through the C ABI with host buffers
     e2e = []
     for _ in range(max(0, min(args.steps, args.e2e_steps))):
@@ -343,6 +362,7 @@ def run_ours(args, rank, ws):
         "phases_s": {"ccsd": ph[0], "lambda": ph[1], "density": ph[2],
                      "contract_dL": ph[3]},
         "peak_device_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
+        "error_estimate": err_est,
         "kernel_classes": classes,
         "ladder": {"seconds_per_step": agg[6][0] / args.steps,
                    "flops_per_step": agg[6][1] / args.steps,
