@@ -16,8 +16,8 @@
 //     pair with error-free TwoSum, so the only rounding is the final
 //     2^-48-level one.  Two accumulator sets alternate so that the drain of
 //     chunk n overlaps the MMAs of chunk n+1.
-// Operands are staged by TMA (64B swizzle, 32 of K per stage) through a
-// 4-stage pipeline; one thread issues tcgen05.mma.kind::f16.  Tile: 128 rows x 64 columns (the
+// Operands are staged by TMA (128B swizzle) through a 2-stage pipeline; one
+// thread issues tcgen05.mma.kind::f16.  Tile: 128 rows x 64 columns (the
 // larger output dimension on the 128-row side); the kernel is persistent
 // (one CTA per SM walks its tiles), so one tile's drain and write overlap
 // the next tile's loads and MMAs.  Every mbarrier wait is bounded and sets
@@ -39,14 +39,12 @@ namespace cdcc {
 
 namespace {
 
-// K per stage: 32 (one 64-byte swizzle row), so that four stages fit in
-// shared memory with four slices and more loads are in flight
-constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 32;
-constexpr int OZ_KBLK_PER_CHUNK = 6;        // exact FP32 chunk: 192 of K
+constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64;
+constexpr int OZ_KBLK_PER_CHUNK = 3;        // exact FP32 chunk: 192 of K
 constexpr int OZ_THREADS = 192;             // 6 warps
 constexpr int OZ_MAXPROB = 8;
 constexpr int OZ_MAXS = 4;
-constexpr int OZ_STAGES = 4;
+constexpr int OZ_STAGES = 2;
 constexpr long long OZ_SPIN_LIMIT = 1LL << 22;
 
 struct OzLaunch {
@@ -117,9 +115,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(512 >> 4) << 32;     // 8 rows x 64 B per core-matrix group
+  d |= (uint64_t)(1024 >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)4 << 61;              // 64-byte swizzle
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -189,7 +187,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int s = L.nslice;
-  constexpr uint32_t A_BYTES = OZ_BM * OZ_BK * 2, B_BYTES = OZ_BN * OZ_BK * 2;
+  constexpr uint32_t A_BYTES = OZ_BM * 128, B_BYTES = OZ_BN * 128;
   const uint32_t stage_bytes = (uint32_t)s * (A_BYTES + B_BYTES);
   uint64_t* full = (uint64_t*)(smem + (size_t)OZ_STAGES * stage_bytes);
   uint64_t* empty = full + OZ_STAGES;
@@ -445,7 +443,7 @@ void oz_map(CUtensorMap* m, const __nv_bfloat16* base, int Kp, int rows, int s,
   CUresult r = oz_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base,
                          dims, strides, box, est,
                          CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
@@ -500,7 +498,7 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->alpha = alpha;
   L->beta = beta;
   L->err = d_err;
-  const int stage = nslice * (OZ_BM + OZ_BN) * OZ_BK * 2;
+  const int stage = nslice * (OZ_BM * 128 + OZ_BN * 128);
   // stages, barriers, and four 32 x 17 double staging tiles for the output
   const int smem = OZ_STAGES * stage + 1024 + 256 + 4 * 32 * 17 * 8;
   cudaFuncSetAttribute(oz_gemm_kernel,
