@@ -91,6 +91,7 @@ struct PermTask {
 
 struct Chunk {
   int task;
+  int len;          // elements of the task this chunk covers (from start)
   int64_t start;
 };
 

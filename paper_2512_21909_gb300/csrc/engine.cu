@@ -326,9 +326,15 @@ const DevTasks& Engine::perm_tasks(const Layout& Y, const Layout& X,
     tasks.push_back(t);
   }
   std::vector<Chunk> chunks;
-  const int CH = chunk_elems();
+  // chunk length: about four CTAs per SM over all tasks (small tensors are
+  // latency bound), between 512 elements and chunk_elems()
+  int64_t total = 0;
+  for (const PermTask& t : tasks) total += t.n;
+  int CH = chunk_elems();
+  while (CH > 512 && total / CH < 4 * 152) CH /= 2;
   for (int i = 0; i < (int)tasks.size(); ++i)
-    for (int64_t s = 0; s < tasks[i].n; s += CH) chunks.push_back({i, s});
+    for (int64_t s = 0; s < tasks[i].n; s += CH)
+      chunks.push_back({i, (int)std::min<int64_t>(CH, tasks[i].n - s), s});
   DevTasks dt;
   dt.ntask = (int)tasks.size();
   dt.nchunk = (int)chunks.size();

@@ -13,6 +13,7 @@ constexpr int CHUNK = 4096;
 
 }  // namespace
 
+// largest chunk of a permutation / update task per CTA
 int chunk_elems() { return CHUNK; }
 
 // ----------------------------------------------------------- permute / axpy
@@ -53,7 +54,7 @@ __global__ void perm_axpy_kernel(const PermTask* __restrict__ tasks,
                                  double beta, double* __restrict__ Y) {
   const Chunk c = chunks[blockIdx.x];
   const PermTask t = tasks[c.task];
-  const int64_t end = min(t.n, c.start + (int64_t)CHUNK);
+  const int64_t end = min(t.n, c.start + (int64_t)c.len);
   int l[MAXRANK];
   for (int64_t e = c.start + threadIdx.x; e < end; e += blockDim.x) {
     int64_t y, x;
@@ -75,7 +76,7 @@ __global__ void jacobi_kernel(const PermTask* __restrict__ tasks,
                               unsigned long long* maxbits) {
   const Chunk c = chunks[blockIdx.x];
   const PermTask t = tasks[c.task];
-  const int64_t end = min(t.n, c.start + (int64_t)CHUNK);
+  const int64_t end = min(t.n, c.start + (int64_t)c.len);
   int l[MAXRANK];
   double mx = 0.0;
   for (int64_t e = c.start + threadIdx.x; e < end; e += blockDim.x) {
