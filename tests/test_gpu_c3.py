@@ -2,14 +2,14 @@
 36 displacements) in the tensor-core schedule with the ladder assembled on
 the fly (the stored ladder integrals alone would be 85 GB).
 
-The dense oracle cannot run at this size; what holds at any size is
-checked instead: the gradient along two displacements equals a central
+The full dense oracle cannot run at this size.  Checked instead: the
+oracle's energy functional and sampled residual rows at the GPU amplitudes
+(oracle.rows), and, as a property that holds at any size, the gradient
+along two displacements against a central
 difference of the GPU's total energy (the library rebuilds h = diag(eps) -
 G(L) from the L it is given, so the prediction adds -sum_pq D_pq dG_pq/dx
 with the one-particle density D the GPU returns; G is quadratic in L and its
-central difference exact).  Step 1e-3; |dg| <= 1e-6.  The amplitude
-equations at full size are checked against the oracle on the C2v workload
-(test_gpu_c2.py).
+central difference exact).  Step 1e-3; |dg| <= 1e-6.
 """
 import numpy as np
 import pytest
@@ -66,3 +66,41 @@ def test_c3_gradient_matches_finite_difference(cd):
         fd = (Ex[0] - Ex[1]) / (2 * step)
         pred = g[x] - float(np.sum(D * (Gx[0] - Gx[1]) / (2 * step)))
         assert abs(pred - fd) <= 1e-6, (x, pred, fd)
+
+
+def test_c3_amplitudes_against_oracle_rows(cd):
+    """At full size the dense oracle cannot solve c3, but it can evaluate
+    its energy functional and sampled residual rows at the GPU amplitudes
+    (oracle.rows): the GPU energy must equal the functional (|dE| <= 1e-9
+    Eh) and the oracle's residual must vanish to the convergence threshold
+    (max |R/D| <= 1e-8) on R1 and on rows R2[i,j,:,:] of pairs inside one
+    irrep and across irreps (occupied irreps: 8,8,8,8,7,7,7,7 orbitals)."""
+    from oracle import rows
+    avail = 0
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    if avail < 120e9:
+        pytest.skip("the dense c3 oracle rows need about 70 GB of host memory")
+    s = make_system(3)
+    o, v = s.nocc, s.nvir
+    ctx = _init(cd, s, s.L)
+    e, _, _ = cd.ccsd_solve(ctx)
+    t1 = T(cd.cdcc_get_amplitudes(ctx, 0, o, v))
+    t2 = T(cd.cdcc_get_amplitudes(ctx, 1, o, v))
+    cd.cd_ccsd_free(ctx)
+    L = T(unpack_dense(s, s.L))
+    h = model.core_from_eps(T(s.eps), L, o)
+    eref = model.e_ref(h, L, o).item()
+    e_or = rows.energy(t1, t2, h, L, o) - eref
+    assert abs(e - e_or) <= 1e-9, (e, e_or)
+    pairs = [(0, 5), (9, 40), (59, 30)]
+    R1, R2 = rows.residual_rows(t1, t2, h, L, o, pairs)
+    eps = s.eps
+    D1 = eps[:o, None] - eps[None, o:]
+    assert np.abs(R1.numpy() / D1).max() <= 1e-8
+    for (i, j) in pairs:
+        Dij = eps[i] + eps[j] - eps[o:, None] - eps[None, o:]
+        r = np.abs(R2[(i, j)].numpy() / Dij).max()
+        assert r <= 1e-8, ((i, j), r)
