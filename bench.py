@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--error-estimate", action="store_true",
                     help="after the timed steps, run cdcc_error_estimate "
                          "(one FP64 residual and density sweep, untimed)")
+    ap.add_argument("--symmetry-ignored", action="store_true",
+                    help="the same data with every irrep label set to 0 "
+                         "(C1 twin): measures the speed-up symmetry gives")
     ap.add_argument("--serving", action="store_true",
                     help="run the serving workload (Poisson arrivals of "
                          "mixed requests) instead of a fixed workload")
@@ -208,6 +211,10 @@ def run_ours(args, rank, ws):
     cdcc.load()
     s = make_system(args.config)
     dL = make_displacements(s)
+    if args.symmetry_ignored:
+        from synth import as_c1
+        s, extra = as_c1(s, list(dL))
+        dL = np.stack(extra)
     nx = dL.shape[0]
     L_d = torch.as_tensor(s.L, device="cuda")
     dL_d = torch.as_tensor(dL, device="cuda")
@@ -353,7 +360,9 @@ def run_ours(args, rank, ws):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t50 * 1e3,
         "p99_s": t99, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD[args.config],
+        "config": {"workload": WORKLOAD[args.config] + (
+                       " (C1 twin: irreps ignored)" if args.symmetry_ignored
+                       else ""),
                    "precision": args.precision,
                    "l2": "flushed between steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
