@@ -71,8 +71,9 @@ typedef enum {
 /* How the particle-particle ladder gets its (ac|bd) integrals.           */
 typedef enum {
     CDCC_LADDER_AUTO = 0,   /* STORED when its estimated footprint is below
-                               40 % of the free device memory at init,
-                               else OTF                                    */
+                               40 % (CDCC_PREC_TC) or 75 % (FP64 and MIXED,
+                               whose on-the-fly build would run in FP64) of
+                               the free device memory at init, else OTF    */
     CDCC_LADDER_STORED = 1, /* (ac|bd) of the undressed vectors built once
                                per gradient and kept in device memory      */
     CDCC_LADDER_OTF = 2     /* assembled from L^P_ab in row batches every

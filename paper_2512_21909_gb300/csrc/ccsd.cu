@@ -950,8 +950,10 @@ void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
       c->otf = false;
     else if (c->opt.ladder == CDCC_LADDER_OTF)
       c->otf = true;
-    else
-      c->otf = stored > 0.4 * (double)fre;
+    else  // with an FP64 finish the on-the-fly build is FP64 DFMA work as
+          // large as the ladder itself, so stored is kept up to 75 %
+      c->otf = stored > (c->opt.precision == CDCC_PREC_TC ? 0.4 : 0.75) *
+                            (double)fre;
     const double gb = c->opt.ladder_batch_gb > 0 ? c->opt.ladder_batch_gb
                                                  : 2.0;
     e.ladder_batch_bytes = (int64_t)(gb * 1e9);
