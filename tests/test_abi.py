@@ -84,3 +84,14 @@ def test_invalid_inputs_rejected_on_host(lib, bad):
     with pytest.raises(cdcc.CdccError) as ei:
         _init(s, **kw)
     assert ei.value.status == cdcc.CDCC_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library the binding raises; there is no CPU path."""
+    from paper_2512_21909_gb300 import cdcc
+    monkeypatch.setattr(cdcc, "_lib", None)
+    monkeypatch.setattr(cdcc, "LIB", str(tmp_path / "absent" / "libcdcc.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        cdcc.load()
+    with pytest.raises(RuntimeError):
+        cdcc.cdcc_default_options()
