@@ -91,6 +91,23 @@ def densities(t1, t2, l1, l2, h, L, o):
     return G.detach(), D.detach(), lag.item()
 
 
+def density_frozen_fock(t1, t2, l1, l2, eps, L, o):
+    """Gamma^P of the FROZEN_FOCK model (the alternative reading of the model
+    Hamiltonian): the Fock matrix stays diag(eps) under a displacement, i.e.
+    h follows L as h(L) = diag(eps) - G(L), and the energy differentiated is
+    the correlation energy:
+        Gamma_FF^P = d/dL [Lag(t, lambda; h(L), L) - E_ref(h(L), L)],
+    symmetrised in pq.  The amplitude and Lambda equations at x = 0 are
+    those of the default model (same h, same L); only Gamma changes."""
+    from .model import core_from_eps, e_ref
+    with torch.enable_grad():
+        Lv = L.detach().clone().requires_grad_(True)
+        hv = core_from_eps(torch.as_tensor(eps, dtype=DT), Lv, o)
+        lag = lagrangian(t1, t2, l1, l2, hv, Lv, o) - e_ref(hv, Lv, o)
+        (gL,) = torch.autograd.grad(lag, (Lv,))
+    return (0.5 * (gL + gL.transpose(1, 2))).detach()
+
+
 def gradient_from_density(G, dL):
     """g_x = sum_P sum_pq Gamma^P_pq dL^P_pq/dx for each displacement x."""
     return torch.einsum("Ppq,xPpq->x", G, dL)

@@ -322,3 +322,36 @@ def test_raw_c0_diverges():
     assert mp2.mp2_energy(s.eps, L, s.nocc) < -30.0
     with pytest.raises(Exception):
         ccsd.solve_ccsd(T(h), T(L), s.nocc, tol=1e-10, maxiter=60, ndiis=0)
+
+
+@pytest.mark.parametrize("which", ["c0", "sym"])
+def test_frozen_fock_gradient_matches_finite_difference(which):
+    """FROZEN_FOCK: f = diag(eps) at every displacement (h rebuilt from L)
+    and E = E_corr; Gamma_FF . dL equals the central difference of E_corr."""
+    if which == "c0":
+        s = make_system(0)
+    else:
+        s = random_system([2, 1, 1, 1], [4, 3, 3, 2], [8, 6, 6, 6], seed=13,
+                          scale=0.35)
+    L, h = _sys_dense(s)
+    o = s.nocc
+    eps = T(s.eps)
+    dL = np.stack([unpack_dense(s, x) for x in make_displacements(s, 2)])
+    r = lagrangian.run_all(h, T(L), o, tol=1e-12, e_tol=1e-13)
+    G = lagrangian.density_frozen_fock(r["cc"]["t1"], r["cc"]["t2"],
+                                       r["lam"]["l1"], r["lam"]["l2"], eps,
+                                       T(L), o)
+    g = lagrangian.gradient_from_density(G, T(dL)).numpy()
+
+    def ecorr(x, d):
+        Lx = T(L + x * d)
+        hx = model.core_from_eps(eps, Lx, o)
+        return ccsd.solve_ccsd(hx, Lx, o, tol=1e-13, e_tol=1e-14)["E_corr"]
+
+    for k in range(2):
+        fd = [(ecorr(st, dL[k]) - ecorr(-st, dL[k])) / (2 * st)
+              for st in (1e-3, 5e-4)]
+        assert abs(g[k] - (4.0 * fd[1] - fd[0]) / 3.0) < 1e-8
+    # and it differs from the default model's gradient (h fixed)
+    g_fc = lagrangian.gradient_from_density(r["G"], T(dL)).numpy()
+    assert np.abs(g - g_fc).max() > 1e-4
