@@ -81,6 +81,19 @@ typedef enum {
                                two batches are resident                    */
 } cdcc_ladder;
 
+/* Model Hamiltonian under a displacement (the MO basis is fixed, there is no
+ * orbital relaxation):
+ *   CDCC_FIXED_CORE   h = diag(eps) - G(L0) stays fixed while L moves; the
+ *                     energy differentiated is E_ref + E_corr (default);
+ *   CDCC_FROZEN_FOCK  the Fock matrix stays diag(eps) (h follows L) and the
+ *                     energy differentiated is E_corr.
+ * Both give the same amplitudes, multipliers and E_corr at the reference
+ * geometry; only Gamma^P (and so the gradient) differs.                    */
+typedef enum {
+    CDCC_FIXED_CORE = 0,
+    CDCC_FROZEN_FOCK = 1
+} cdcc_fock_model;
+
 typedef void *(*cdcc_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*cdcc_free_fn)(void *ptr, size_t bytes, void *stream,
                              void *user);
@@ -100,6 +113,7 @@ typedef struct {
     void *alloc_user;
     int ladder;             /* cdcc_ladder (default CDCC_LADDER_AUTO)       */
     double ladder_batch_gb; /* OTF: GB of one (ab|cd) row batch (default 2) */
+    int fock_model;         /* cdcc_fock_model (default CDCC_FIXED_CORE)    */
 } cdcc_options;
 
 typedef struct cdcc_ctx cdcc_ctx;

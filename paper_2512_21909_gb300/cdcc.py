@@ -24,6 +24,7 @@ STATUS = {0: "CDCC_OK", 1: "CDCC_EINVAL", 2: "CDCC_ENOMEM", 3: "CDCC_ENOCONV",
           7: "CDCC_ETIMEOUT"}
 PREC_FP64, PREC_MIXED, PREC_TC = 0, 1, 2
 LADDER_AUTO, LADDER_STORED, LADDER_OTF = 0, 1, 2
+FIXED_CORE, FROZEN_FOCK = 0, 1
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
                             ctypes.c_void_p)
@@ -38,7 +39,8 @@ class cdcc_options(ctypes.Structure):
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("ladder", ctypes.c_int),
-                ("ladder_batch_gb", ctypes.c_double)]
+                ("ladder_batch_gb", ctypes.c_double),
+                ("fock_model", ctypes.c_int)]
 
 
 class CdccError(RuntimeError):

@@ -633,6 +633,7 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
 }
 
 void assemble_density(cdcc_ctx* c);
+void frozen_fock_correction(cdcc_ctx* c);
 
 void run_density(cdcc_ctx* c, double* D1) {
   Engine& e = *c->eng;
@@ -643,6 +644,7 @@ void run_density(cdcc_ctx* c, double* D1) {
              TAG_L | TAG_H);
   e.set_precision(0);
   assemble_density(c);
+  if (c->opt.fock_model == CDCC_FROZEN_FOCK) frozen_fock_correction(c);
   pt.stop();
   if (D1) {
     const int n = c->hd.n;
@@ -653,6 +655,63 @@ void run_density(cdcc_ctx* c, double* D1) {
     std::memcpy(D1, dense.data(), dense.size() * 8);
   }
   c->state = 4;
+}
+
+// FROZEN_FOCK model: the Fock matrix stays diag(eps) under a displacement
+// (h follows L as h = diag(eps) - G(L)) and E = E_corr, so
+//     Gamma_FF = Gamma - d<M, G(L)>/dL,   M = D - 1_occ,
+// with D the symmetrised one-particle density of the density sweep and
+// G(L) = 2 L^P J_P - sum_k L^P_pk L^P_kq the two-electron Fock part (the
+// 1_occ removes the reference energy sum_i (2 eps_i - G_ii)).  d<M,G>/dL
+// comes from the engine's reverse sweep over a short recorded evaluation of
+// <M, G(L)>; the recorded Lambda/density tape is replaced and rebuilt when
+// next needed.
+void frozen_fock_correction(cdcc_ctx* c) {
+  Engine& e = *c->eng;
+  Tensor *Loo = c->Loo, *Lov = c->Lov, *Lvo = c->Lvo, *Lvv = c->Lvv;
+  Tensor* Moo = e.tensor("ff_Moo", {SO, SO}, 1);
+  Tensor* Mov = e.tensor("ff_Mov", {SO, SV}, 1);
+  Tensor* Mvo = e.tensor("ff_Mvo", {SV, SO}, 1);
+  Tensor* Mvv = e.tensor("ff_Mvv", {SV, SV}, 1);
+  e.axpy(1.0, c->D1s, "pq", 0.0, Moo, "pq");
+  e.axpy(-1.0, c->Ioo, "ij", 1.0, Moo, "ij");
+  e.axpy(1.0, c->D1s, "pq", 0.0, Mov, "pq");
+  e.axpy(1.0, c->D1s, "pq", 0.0, Mvo, "pq");
+  e.axpy(1.0, c->D1s, "pq", 0.0, Mvv, "pq");
+  e.clear_tape();
+  c->tape_ready = false;
+  e.record(true);
+  Tensor* J = e.tensor("ff_J", {SQ}, 1);
+  e.contract(1.0, Loo, "Pkl", c->Ioo, "kl", 0.0, J, "P");
+  Tensor* Goo = e.tensor("ff_Goo", {SO, SO}, 1);
+  e.contract(2.0, Loo, "Pij", J, "P", 0.0, Goo, "ij");
+  e.contract(-1.0, Loo, "Pik", Loo, "Pkj", 1.0, Goo, "ij");
+  Tensor* Gov = e.tensor("ff_Gov", {SO, SV}, 1);
+  e.contract(2.0, Lov, "Pia", J, "P", 0.0, Gov, "ia");
+  e.contract(-1.0, Loo, "Pik", Lov, "Pka", 1.0, Gov, "ia");
+  Tensor* Gvo = e.tensor("ff_Gvo", {SV, SO}, 1);
+  e.contract(2.0, Lvo, "Pai", J, "P", 0.0, Gvo, "ai");
+  e.contract(-1.0, Lvo, "Pak", Loo, "Pki", 1.0, Gvo, "ai");
+  Tensor* Gvv = e.tensor("ff_Gvv", {SV, SV}, 1);
+  e.contract(2.0, Lvv, "Pab", J, "P", 0.0, Gvv, "ab");
+  e.contract(-1.0, Lvo, "Pak", Lov, "Pkb", 1.0, Gvv, "ab");
+  Tensor* EG = e.tensor("ff_EG", {}, 0);
+  e.contract(1.0, Moo, "ij", Goo, "ij", 0.0, EG, "");
+  e.contract(1.0, Mov, "ia", Gov, "ia", 1.0, EG, "");
+  e.contract(1.0, Mvo, "ai", Gvo, "ai", 1.0, EG, "");
+  e.contract(1.0, Mvv, "ab", Gvv, "ab", 1.0, EG, "");
+  e.record(false);
+  e.backward({{EG, nullptr}}, TAG_L);
+  e.clear_tape();
+  // Gsym -= sym(d<M,G>/dL), assembled like Gamma^P
+  Tensor* Dg = e.tensor("ff_dG", {SQ, SA, SA}, 1);
+  e.zero(Dg);
+  e.axpy(1.0, e.adjoint(Loo), "Pij", 1.0, Dg, "Pij");
+  e.axpy(1.0, e.adjoint(Lov), "Pia", 1.0, Dg, "Pia");
+  e.axpy(1.0, e.adjoint(Lvo), "Pai", 1.0, Dg, "Pai");
+  e.axpy(1.0, e.adjoint(Lvv), "Pab", 1.0, Dg, "Pab");
+  e.axpy(-0.5, Dg, "Ppq", 1.0, c->Gsym, "Ppq");
+  e.axpy(-0.5, Dg, "Pqp", 1.0, c->Gsym, "Ppq");
 }
 
 // Gamma^P and D from the adjoints left by the density sweep.
@@ -774,6 +833,7 @@ void run_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}},
              TAG_L | TAG_H);
   assemble_density(c);
+  if (c->opt.fock_model == CDCC_FROZEN_FOCK) frozen_fock_correction(c);
   if (nx > 0) run_contract(c, nx, x_irrep, dL, g64.data());
   for (int x = 0; x < nx; ++x) dg[x] = std::fabs(g64[x] - g0[x]);
   CK(cudaMemcpyAsync(c->Gsym->d, keepG->d, (size_t)ng * 8,
@@ -1067,6 +1127,7 @@ void cdcc_default_options(cdcc_options* o) {
   o->stream = nullptr;
   o->ladder = CDCC_LADDER_AUTO;
   o->ladder_batch_gb = 2.0;
+  o->fock_model = CDCC_FIXED_CORE;
 }
 
 cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
@@ -1084,8 +1145,11 @@ cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
   if (c->opt.max_iter <= 0) c->opt.max_iter = 100;
   cdcc_status s = guarded(c, [&] {
     if (c->opt.precision < CDCC_PREC_FP64 || c->opt.precision > CDCC_PREC_TC ||
-        c->opt.ladder < CDCC_LADDER_AUTO || c->opt.ladder > CDCC_LADDER_OTF)
-      throw StatusError(CDCC_EINVAL, "unknown precision or ladder mode");
+        c->opt.ladder < CDCC_LADDER_AUTO || c->opt.ladder > CDCC_LADDER_OTF ||
+        c->opt.fock_model < CDCC_FIXED_CORE ||
+        c->opt.fock_model > CDCC_FROZEN_FOCK)
+      throw StatusError(CDCC_EINVAL,
+                        "unknown precision, ladder mode or Fock model");
     init_ctx(c, nirrep, nocc, nvir, nchol, orb_irrep, eps, chol_irrep, L);
   });
   *out = c;  // also on error, so that cdcc_last_error can be read

@@ -130,6 +130,29 @@ def test_bounded_wait_gives_up_and_device_stays_usable(cd):
     assert np.isfinite(e) and np.all(np.isfinite(g))
 
 
+@pytest.mark.parametrize("which", ["c0", "ragged"])
+def test_frozen_fock_matches_oracle(cd, which):
+    """cdcc_options.fock_model = FROZEN_FOCK (Fock matrix kept at diag(eps)
+    under a displacement, E = E_corr) against the oracle's Gamma_FF, which
+    its own finite-difference pin fixes."""
+    if which == "c0":
+        s = make_system(0)
+    else:
+        s = random_system([3, 2], [7, 5], [11, 9], seed=103, scale=0.45)
+    dL = make_displacements(s, 3)
+    L = torch.as_tensor(unpack_dense(s, s.L))
+    h = model.core_from_eps(torch.as_tensor(s.eps), L, s.nocc)
+    r = lagrangian.run_all(h, L, s.nocc, tol=1e-12, e_tol=1e-13)
+    Gff = lagrangian.density_frozen_fock(r["cc"]["t1"], r["cc"]["t2"],
+                                         r["lam"]["l1"], r["lam"]["l2"],
+                                         s.eps, L, s.nocc)
+    G_or = pack_dense(s, Gff.numpy())
+    gg = gpu_run(cd, s, dL, fock_model=cd.FROZEN_FOCK)
+    assert abs(gg["e"] - r["cc"]["E_corr"]) < 1e-10
+    assert np.abs(gg["G"] - G_or).max() < 1e-9
+    assert np.abs(gg["g"] - dL @ G_or).max() < 1e-9
+
+
 def test_raw_c0_divergence_is_reported(cd):
     """c0 with the literal Cholesky distribution (s = 1, E_MP2 = -37 Eh) is
     the strong-correlation stress case: the oracle's CCSD diverges on it
