@@ -109,3 +109,20 @@ def test_ladder_policy_depends_on_size_only():
     assert srv.ladder_for(big) == cdcc.LADDER_OTF
     f_st = footprint(big, cdcc.PREC_TC, cdcc.LADDER_STORED)
     assert f_st["w"] == 40 ** 4 and f_st["t2"] == 16 * 1600
+
+
+class FailingServer(FakeServer):
+    def execute(self, req, slot):
+        if req.index == 2:
+            raise cdcc.CdccError(cdcc.CDCC_ENUMERIC, "fake divergence")
+        return super().execute(req, slot)
+
+
+def test_other_failures_are_reported_per_request():
+    reqs = [_req(i, 0.0) for i in range(5)]
+    srv = FailingServer(max_active=2, budget_bytes=1 << 50)
+    srv.run(reqs, realtime=False)
+    assert reqs[2].status.startswith("error")
+    assert all(r.status == "done" for k, r in enumerate(reqs) if k != 2)
+    st = latency_stats(reqs, srv.wall)
+    assert st["done"] == 4 and st["failed"] == 1
