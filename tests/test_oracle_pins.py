@@ -355,3 +355,23 @@ def test_frozen_fock_gradient_matches_finite_difference(which):
     # and it differs from the default model's gradient (h fixed)
     g_fc = lagrangian.gradient_from_density(r["G"], T(dL)).numpy()
     assert np.abs(g - g_fc).max() > 1e-4
+
+
+def test_rows_equal_full_residual_on_a_larger_symmetric_case():
+    """Beyond brute-force sizes: oracle.rows reproduces every row of the
+    (brute-force-pinned) full residual on a D2h case with ragged irreps."""
+    s = random_system([2, 1, 1, 1, 1, 0, 1, 0], [5, 4, 3, 3, 2, 3, 2, 2],
+                      [9, 7, 7, 6, 6, 6, 6, 5], seed=77, scale=0.4)
+    L = T(unpack_dense(s, s.L))
+    h = model.core_from_eps(T(s.eps), L, s.nocc)
+    o, v = s.nocc, s.nvir
+    rng = np.random.default_rng(77)
+    t1 = T(rng.standard_normal((o, v)) * 0.05)
+    t2 = T(rng.standard_normal((o, o, v, v)) * 0.05)
+    R1f, R2f, Ef = ccsd.residual(t1, t2, h, L, o)
+    assert abs(rows.energy(t1, t2, h, L, o) - Ef.item()) < 1e-12
+    pairs = [(i, j) for i in range(o) for j in range(o)]
+    R1, R2 = rows.residual_rows(t1, t2, h, L, o, pairs)
+    assert (R1 - R1f).abs().max().item() < 1e-12
+    for (i, j) in pairs:
+        assert (R2[(i, j)] - R2f[i, j]).abs().max().item() < 1e-12
