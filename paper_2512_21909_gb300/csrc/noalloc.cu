@@ -19,6 +19,7 @@
 // call, so nothing has to be cleared between calls.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "../../include/cdcc.h"
@@ -26,7 +27,9 @@
 namespace {
 
 constexpr int NA_THREADS = 256;
-constexpr int NA_MAX_BLOCKS = 1216;   // 152 SMs x 8
+// capacity of the fixed partial-sum array in CTAs; a call launches
+// min(8 x the device's SM count, this) CTAs (1216 on a 152-SM GB300)
+constexpr int NA_MAX_BLOCKS = 2048;
 constexpr int NA_XPASS = 8;           // displacements per pass
 
 static __device__ __align__(256) double
@@ -85,13 +88,17 @@ __global__ void na_finish_kernel(const double* __restrict__ partial, int nblk,
   }
 }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (the current one), or managed memory.  A
+// pointer into another GPU's memory is rejected: without peer access the
+// kernels would fault on it.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     (void)cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -102,11 +109,14 @@ extern "C" cdcc_status cdcc_contract_dL_noalloc(const double* gamma,
                                                 void* stream) {
   if (!gamma || !dL || !g || nnz == 0) return CDCC_EINVAL;
   if (nx < 1 || nx > CDCC_NOALLOC_MAX_NX) return CDCC_EINVAL;
-  if (!on_device(gamma) || !on_device(dL) || !on_device(g))
-    return CDCC_EINVAL;
+  // an error left pending by earlier work is not this call's: report it
+  // without clearing it, so that the caller's own check still sees it
+  if (cudaPeekAtLastError() != cudaSuccess) return CDCC_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES)
     return CDCC_ECUDA;
+  if (!on_device(gamma, dev) || !on_device(dL, dev) || !on_device(g, dev))
+    return CDCC_EINVAL;
   double* partial = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mutex);
@@ -121,15 +131,35 @@ extern "C" cdcc_status cdcc_contract_dL_noalloc(const double* gamma,
     }
     partial = g_na_ptr[dev];
   }
+  // the stream must belong to the current device as well (0 = legacy
+  // default stream of the current device)
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (st) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return CDCC_EINVAL;
+    }
+    if (sdev != dev) return CDCC_EINVAL;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+          cudaSuccess ||
+      sms <= 0) {
+    (void)cudaGetLastError();
+    return CDCC_ECUDA;
+  }
+  const long long cap = std::min<long long>(NA_MAX_BLOCKS, 8LL * sms);
   long long blocks = ((long long)nnz + 4095) / 4096;
-  if (blocks > NA_MAX_BLOCKS) blocks = NA_MAX_BLOCKS;
+  if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   const long long per = ((long long)nnz + blocks - 1) / blocks;
-  for (int x0 = 0; x0 < nx; x0 += NA_XPASS)
+  for (int x0 = 0; x0 < nx; x0 += NA_XPASS) {
     na_dot_kernel<<<(int)blocks, NA_THREADS, 0, st>>>(gamma, dL, x0, nx,
                                                       (long long)nnz, per,
                                                       partial);
+    if (cudaGetLastError() != cudaSuccess) return CDCC_ECUDA;
+  }
   na_finish_kernel<<<nx, 256, 0, st>>>(partial, (int)blocks, g);
   return cudaGetLastError() == cudaSuccess ? CDCC_OK : CDCC_ECUDA;
 }
