@@ -70,7 +70,9 @@ def dressed_fock(hh, Lh, o):
             - einsum("Ppk,Pkq->pq", Lh[:, :, :o], Lh[:, :o, :]))
 
 
-def _ladder_block(t2, vv, a0: int, a1: int):
+def ladder_block(t2, vv, a0: int, a1: int):
+    """Rows a0 <= a < a1 of the ladder: (ac|bd) for that block of a, then
+    sum_cd t[i,j,c,d] (ac|bd)."""
     W = einsum("Pac,Pbd->acbd", vv[:, a0:a1], vv)        # (ac|bd), a in block
     return einsum("ijcd,acbd->ijab", t2, W)
 
@@ -82,15 +84,15 @@ def ladder(t2, vv):
         return torch.zeros_like(t2)
     blk = max(1, min(v, int(2.0e7 // max(1, v ** 3))))
     if blk >= v:
-        return _ladder_block(t2, vv, 0, v)
+        return ladder_block(t2, vv, 0, v)
     parts = []
     for a0 in range(0, v, blk):
         a1 = min(v, a0 + blk)
         if torch.is_grad_enabled():
-            parts.append(checkpoint(_ladder_block, t2, vv, a0, a1,
+            parts.append(checkpoint(ladder_block, t2, vv, a0, a1,
                                     use_reentrant=False))
         else:
-            parts.append(_ladder_block(t2, vv, a0, a1))
+            parts.append(ladder_block(t2, vv, a0, a1))
     return torch.cat(parts, dim=2)
 
 

@@ -5,7 +5,7 @@ Sec. 2.1 Eq. 1:  (pq|rs) = sum_P L^P_pq L^P_rs.
 
 The paper works with AO integrals, SCF orbitals and orbital relaxation
 (Sec. 2.5); the synthetic workloads have none of these.  Reading adopted
-(listed in DESIGN.md as "model Hamiltonian"):
+for the model Hamiltonian:
   * the core Hamiltonian is fixed so that at the reference geometry the
     closed-shell Fock matrix is diag(eps):
         h_pq = eps_p delta_pq - sum_k [ 2 (pq|kk) - (pk|kq) ]

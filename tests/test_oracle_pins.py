@@ -375,3 +375,30 @@ def test_rows_equal_full_residual_on_a_larger_symmetric_case():
     assert (R1 - R1f).abs().max().item() < 1e-12
     for (i, j) in pairs:
         assert (R2[(i, j)] - R2f[i, j]).abs().max().item() < 1e-12
+
+
+# ------------------------------------------- workload energy scales (s_cfg)
+@pytest.mark.parametrize("occ,vir,chol,seed", [((3,), (9,), (14,), 21),
+                                               ((2, 1, 2, 0), (4, 3, 3, 2),
+                                                (6, 4, 5, 3), 22)])
+def test_scale_calibration_mp2_equals_closed_form(occ, vir, chol, seed):
+    # the calibration script's chunked MP2 over the packed L_ov block equals
+    # the closed-form MP2 energy on the dense vectors (C1 and symmetric)
+    from oracle import calibrate_scale
+    s = random_system(list(occ), list(vir), list(chol), seed=seed, scale=0.7)
+    L = unpack_dense(s, s.L)
+    e_closed = mp2.mp2_energy(s.eps, L, s.nocc)
+    Lov = calibrate_scale._ov_dense(s)
+    assert np.array_equal(Lov, L[:, :s.nocc, s.nocc:])
+    e_chunk = calibrate_scale.mp2_chunked(s.eps, Lov)
+    assert abs(e_chunk - e_closed) <= 1e-12 * abs(e_closed)
+
+
+def test_stored_scale_gives_target_mp2_energy():
+    # E_MP2 is homogeneous of degree 4 in L, so the stored s_cfg of the
+    # smallest workload must reproduce the target -0.04 Eh per occupied
+    # orbital with the closed form on the scaled arrays
+    s = make_system(0)
+    L = unpack_dense(s, s.L)
+    e = mp2.mp2_energy(s.eps, L, s.nocc)
+    assert abs(e - (-0.04 * s.nocc)) < 1e-10
