@@ -4,12 +4,20 @@ One step = one full gradient: cd_ccsd_init (inputs already in HBM) ->
 ccsd_solve -> lambda_solve -> build_density -> contract_dL over all
 displacements, through the C ABI.  Prints ONE JSON line (rank 0).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1]
-                    [--precision fp64|mixed] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 3]
+                    [--precision tc|mixed|fp64] [--compare 2|none]
+                    [--impl ours|reference]
+    python bench.py --gemm M,N,K[,ta,tb] [--gemm-modes 0,2,14]
 
+Default workload: D2h o=60 v=540 nL=2400 with 36 displacements in the
+tensor-core schedule (BF16x3 iterations, exact-slice accurate phase).  The
+mixed-vs-FP64 comparison runs on the C2v o=40 v=360 nL=1600 workload (the
+FP64 path would take about half an hour on the larger one).
 --impl reference times the FP64 CPU oracle (bounded sample, host cores).
 With N > 1 (torchrun) every rank runs an independent replica (the method
 does not shard across GPUs here); value is the max over ranks.
+--gemm times the library's contraction kernels on one product shape
+through cdcc_dgemm (the command the kernel profiles were taken with).
 """
 from __future__ import annotations
 
@@ -32,7 +40,15 @@ WORKLOAD = {0: "c0: C1 o=4 v=20 nL=60, 6 displacements",
             1: "c1: D2h o=16 v=144 nL=640, 18 displacements",
             2: "c2: C2v o=40 v=360 nL=1600, 24 displacements",
             3: "c3: D2h o=60 v=540 nL=2400, 36 displacements"}
-FP64_PEAK_GFLOPS = 1250.0      # GB300 FP64 nominal (profiling recipe table)
+DTYPE = {"fp64": "f64", "mixed": "bf16x3+f64", "tc": "bf16x3+exact-slice"}
+# FP64 pipe of GB300 (not in the measured peaks): 2 DFMA per clock per SM
+# x 2 flop x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+CLASSES = ["gemm64", "permute", "update", "contract_dL", "other",
+           "tc_float_slices", "tc_exact_slices"]
+# BF16 MMAs per algorithmic product: float slices (2 slices: i + j < 2) and
+# exact slices (4 slices: i + j < 4)
+MMA_PER_PRODUCT = {"tc_float_slices": 3, "tc_exact_slices": 10}
 
 
 def parse():
@@ -40,15 +56,21 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--config", type=int, default=1)
-    ap.add_argument("--precision", default="fp64",
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--precision", default="tc",
                     choices=["fp64", "mixed", "tc"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--others", default="all",
-                    help="other schedules to time beside --precision: "
+    ap.add_argument("--compare", default="2",
+                    help="workload of the mixed-vs-FP64 comparison (both "
+                         "schedules timed once each), or 'none'")
+    ap.add_argument("--others", default="none",
+                    help="other schedules timed on the --config workload: "
                          "'all', 'none' or a comma list")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-linearize", action="store_true",
+                    help="every accurate-phase iteration fully accurate "
+                         "(cdcc_options.ladder_linearize = 0)")
     ap.add_argument("--error-estimate", action="store_true",
                     help="after the timed steps, run cdcc_error_estimate "
                          "(one FP64 residual and density sweep, untimed)")
@@ -60,6 +82,11 @@ def parse():
                          "mixed requests) instead of a fixed workload")
     ap.add_argument("--jobs", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--gemm", default=None,
+                    help="M,N,K[,ta,tb]: time cdcc_dgemm on one shape")
+    ap.add_argument("--gemm-modes", default="0,2,14")
+    ap.add_argument("--ref-blocks", type=int, default=1,
+                    help="oracle ladder blocks timed per reference step")
     return ap.parse_args()
 
 
@@ -76,6 +103,21 @@ def barrier(ws):
 def allmax(x, ws):
     from paper_2512_21909_gb300 import replicas
     return replicas.allmax(x, ws)
+
+
+def peaks():
+    """Roofline denominators: MEASURED_PEAKS.json if present, else the
+    earlier GB300 measurement of the profiling notes (labelled)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]),
+                "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -136,61 +178,96 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(cfg):
-    """Time the FP64 oracle on a bounded sample of the workload: one CCSD
-    residual and one Lambda (reverse-mode) evaluation at the MP2-like start,
-    scaled by the oracle's own iteration counts stored with the golden
-    values (tests/golden/c<cfg>.json, written by oracle-only code)."""
-    import torch
-    from synth import make_system, unpack_dense
-    from oracle import model, ccsd, lagrangian
-    s = make_system(cfg)
-    o, v = s.nocc, s.nvir
-    L = torch.as_tensor(unpack_dense(s, s.L))
-    h = model.core_from_eps(torch.as_tensor(s.eps), L, o)
-    z1 = torch.zeros(o, v, dtype=torch.float64)
-    z2 = torch.zeros(o, o, v, v, dtype=torch.float64)
-    t0 = time.perf_counter()
-    with torch.no_grad():
-        R1, R2, _ = ccsd.residual(z1, z2, h, L, o)
-    t_cc = time.perf_counter() - t0
-    f = model.fock(h, L, o)
-    _, Dijab = ccsd.denominators(f, o)
-    t2 = R2 / Dijab
-    t0 = time.perf_counter()
-    lagrangian.lambda_gradient(z1, t2, z1, t2, h, L, o)
-    t_lam = time.perf_counter() - t0
-    gold = os.path.join(ROOT, "tests", "golden", f"c{cfg}.json")
-    n_cc, n_lam = 17, 15
-    if os.path.exists(gold):
-        g = json.load(open(gold))
-        n_cc, n_lam = g["ccsd_iterations"], g["lambda_iterations"]
-    est = n_cc * t_cc + (n_lam + 1) * t_lam     # +1: density sweep
-    return dict(value=est, unit="s", cores=torch.get_num_threads(),
-                kind="oracle",
-                sample=(f"1 CCSD residual ({t_cc:.2f}s) + 1 Lambda "
-                        f"reverse sweep ({t_lam:.2f}s) of {WORKLOAD[cfg]}, "
-                        f"scaled by the oracle's {n_cc} CCSD + {n_lam} "
-                        "Lambda iterations + 1 density sweep"),
-                sample_seconds=t_cc + t_lam)
+class OracleSample:
+    """The FP64 oracle on a bounded sample of a workload.
+
+    The oracle's rate-determining step is its particle-particle ladder
+    (Sec. 2.3), evaluated one block of the virtual index a at a time
+    (oracle.ccsd.ladder_block: (ac|bd) for the block from L^P_ab, then the
+    product with t2); the whole ladder is n_blocks such blocks.  A sample
+    times `blocks` of them on the dense (symmetry-ignored) arrays of the
+    workload and scales to a full gradient:
+        t_grad = t_block * n_blocks * n_ladder,
+        n_ladder = n_cc + 4 (n_lambda + 1),
+    n_cc / n_lambda the iteration counts of the oracle's own c1 run
+    (tests/golden/c1.json; 17 and 15): one ladder per CCSD residual and
+    about four ladder-equivalents per reverse-mode Lambda or density sweep
+    (checkpointed forward, recomputation and the two adjoint products).
+    The oracle's O(o^3 v^3) terms are not counted, so this is a lower
+    bound of the oracle's time-to-gradient."""
+
+    def __init__(self, cfg):
+        import torch
+        from synth import make_system, unpack_dense
+        s = make_system(cfg)
+        o, v = s.nocc, s.nvir
+        L = unpack_dense(s, s.L)
+        self.vv = torch.as_tensor(np.ascontiguousarray(L[:, o:, o:]))
+        del L
+        rng = np.random.default_rng(20251221909 + 100 + cfg)
+        t2 = rng.standard_normal((o, o, v, v)) * 1e-3
+        self.t2 = torch.as_tensor(t2)
+        self.o, self.v, self.cfg = o, v, cfg
+        self.blk = max(1, min(v, int(2.0e7 // max(1, v ** 3))))
+        self.n_blocks = -(-v // self.blk)
+        gold = os.path.join(ROOT, "tests", "golden", "c1.json")
+        self.n_cc, self.n_lam = 17, 15
+        if os.path.exists(gold):
+            g = json.load(open(gold))
+            self.n_cc = g["ccsd_iterations"]
+            self.n_lam = g["lambda_iterations"]
+        self.n_ladder = self.n_cc + 4 * (self.n_lam + 1)
+        self.next_a = 0
+        self.threads = torch.get_num_threads()
+
+    def time_blocks(self, nblocks):
+        import torch
+        from oracle import ccsd
+        t = 0.0
+        with torch.no_grad():
+            for _ in range(nblocks):
+                a0 = self.next_a
+                a1 = min(self.v, a0 + self.blk)
+                self.next_a = a1 % self.v
+                t0 = time.perf_counter()
+                ccsd.ladder_block(self.t2, self.vv, a0, a1)
+                t += time.perf_counter() - t0
+        return t / nblocks
+
+    def estimate(self, nblocks):
+        tb = self.time_blocks(nblocks)
+        est = tb * self.n_blocks * self.n_ladder
+        return dict(
+            value=est, unit="s", cores=self.threads, kind="oracle",
+            sample=(f"{nblocks} of the {self.n_blocks} a-blocks of the "
+                    f"oracle's particle-particle ladder on {WORKLOAD[self.cfg]}"
+                    f" (oracle.ccsd.ladder_block, dense FP64, {tb:.2f} s per "
+                    f"block), scaled by {self.n_blocks} blocks x "
+                    f"{self.n_ladder} ladder evaluations ({self.n_cc} CCSD + "
+                    f"4 x ({self.n_lam} Lambda + 1 density)); O(o^3 v^3) "
+                    "terms not counted (lower bound)"),
+            seconds_per_block=tb, sample_seconds=tb * nblocks)
 
 
 def run_reference(args, rank, ws):
     if rank != 0:
         return
-    times = []
+    smp = OracleSample(args.config)
+    smp.time_blocks(1)                   # untimed warm-up (thread pools)
+    vals = []
     for i in range(args.warmup + args.steps):
-        r = oracle_sample(args.config)
+        r = smp.estimate(args.ref_blocks)
         if i >= args.warmup:
-            times.append(r["value"])
-    v = float(np.median(times))
+            vals.append(r["value"])
+    v = float(np.median(vals))
     r["value"] = v
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": v * 1e3, "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD[args.config],
-                                           "precision": "fp64"},
+           "ms_per_step": v * 1e3, "p99_s": float(np.percentile(vals, 99)),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD[args.config],
+                      "precision": "fp64 (CPU oracle)"},
            "cpu_baseline": r,
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
@@ -198,9 +275,128 @@ def run_reference(args, rank, ws):
 
 
 # ---------------------------------------------------------------- GPU arm
+def prec_code(cdcc, name):
+    return {"fp64": cdcc.PREC_FP64, "mixed": cdcc.PREC_MIXED,
+            "tc": cdcc.PREC_TC}[name]
+
+
+class Runner:
+    """One workload resident in HBM; one() runs a full gradient."""
+
+    def __init__(self, cfg, dev, symmetry_ignored=False):
+        import torch
+        from synth import make_system, make_displacements
+        s = make_system(cfg)
+        dL = make_displacements(s)
+        if symmetry_ignored:
+            from synth import as_c1
+            s, extra = as_c1(s, list(dL))
+            dL = np.stack(extra)
+        self.s, self.dL, self.nx, self.dev = s, dL, dL.shape[0], dev
+        self.L_d = torch.as_tensor(s.L, device="cuda")
+        self.dL_d = torch.as_tensor(dL, device="cuda")
+        self._host = None
+
+    def host(self):
+        import torch
+        if self._host is None:
+            self._host = (torch.as_tensor(self.s.L).pin_memory(),
+                          torch.as_tensor(self.dL).pin_memory())
+        return self._host
+
+    def one(self, cdcc, prec, Lsrc=None, dLsrc=None, profile=False,
+            linearize=True):
+        s = self.s
+        o = cdcc.cdcc_default_options()
+        o.device = self.dev
+        o.precision = prec_code(cdcc, prec)
+        o.ladder_linearize = 1 if linearize else 0
+        ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
+                                s.orb_irrep, s.eps, s.chol_irrep,
+                                self.L_d if Lsrc is None else Lsrc, options=o)
+        if profile:
+            cdcc.cdcc_profile(ctx, True)
+        e, g = cdcc.gradient(ctx, self.dL_d if dLsrc is None else dLsrc)
+        info = {"launches": cdcc.cdcc_kernel_launches(ctx),
+                "phases": [float(x) for x in cdcc.cdcc_phase_times(ctx)],
+                "solver": [int(x) for x in cdcc.cdcc_solver_info(ctx)]}
+        if profile:
+            info["stats"] = [cdcc.cdcc_kernel_stats(ctx, k)
+                             for k in range(len(CLASSES))]
+            info["ladder"] = cdcc.cdcc_ladder_stats(ctx)
+        cdcc.cd_ccsd_free(ctx)
+        return e, g, info
+
+
+def timed_steps(torch, runner, cdcc, prec, n, flush, stream, linearize):
+    times, infos, last = [], [], None
+    for _ in range(n):
+        flush.fill_(1.0)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        e, g, info = runner.one(cdcc, prec, profile=True, linearize=linearize)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1) * 1e-3)
+        infos.append(info)
+        last = (e, g)
+    return times, infos, last
+
+
+def class_table(infos, steps):
+    agg = np.zeros((len(CLASSES), 3))
+    lad = np.zeros(3)
+    for inf in infos:
+        agg += np.array(inf["stats"], dtype=float)
+        lad += np.array(inf["ladder"], dtype=float)
+    out = {}
+    for k, nm in enumerate(CLASSES):
+        sec, n, w = agg[k] / steps
+        out[nm] = {"seconds": sec, "launches": int(round(n)),
+                   "work_per_step": w}
+    return out, lad / steps
+
+
+def rooflines(classes, pk):
+    """Per kernel class: achieved rate over its device time against its
+    bound.  Tensor-core classes: algorithmic flops (2MNK) and the BF16 MMA
+    work they execute (x3 float slices, x10 exact slices) against the
+    measured sustained BF16 peak; FP64 GEMM against the derived DFMA peak;
+    the rest (bytes) against the measured HBM copy bandwidth."""
+    out = {}
+    for nm, c in classes.items():
+        sec, work = c["seconds"], c["work_per_step"]
+        if sec <= 0:
+            continue
+        if nm in MMA_PER_PRODUCT:
+            alg = work / sec / 1e12
+            exe = alg * MMA_PER_PRODUCT[nm]
+            P = pk["bf16_tflops_sustained"]
+            out[nm] = {"bound": "tensor", "achieved": alg, "peak": P,
+                       "unit": "TFLOP/s", "frac": alg / P,
+                       "executed_mma_tflops": exe, "frac_executed": exe / P,
+                       "peak_source": pk["source"] + " bf16 sustained",
+                       "seconds": sec}
+        elif nm == "gemm64":
+            a = work / sec / 1e12
+            out[nm] = {"bound": "alu", "achieved": a,
+                       "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": a / FP64_PEAK_TFLOPS,
+                       "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x "
+                                      "152 SMs x 2.07 GHz",
+                       "seconds": sec}
+        else:
+            a = work / sec / 1e9
+            out[nm] = {"bound": "hbm", "achieved": a, "peak": pk["hbm_gbs"],
+                       "unit": "GB/s", "frac": a / pk["hbm_gbs"],
+                       "peak_source": pk["source"] + " HBM copy",
+                       "seconds": sec}
+    return out
+
+
 def run_ours(args, rank, ws):
     import torch
-    from synth import make_system, make_displacements
     from paper_2512_21909_gb300 import build as cbuild, cdcc
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
@@ -209,46 +405,17 @@ def run_ours(args, rank, ws):
         cbuild.build()
     barrier(ws)
     cdcc.load()
-    s = make_system(args.config)
-    dL = make_displacements(s)
-    if args.symmetry_ignored:
-        from synth import as_c1
-        s, extra = as_c1(s, list(dL))
-        dL = np.stack(extra)
-    nx = dL.shape[0]
-    L_d = torch.as_tensor(s.L, device="cuda")
-    dL_d = torch.as_tensor(dL, device="cuda")
-    L_h = torch.as_tensor(s.L).pin_memory()
-    dL_h = torch.as_tensor(dL).pin_memory()
+    pk = peaks()
+    lin = not args.no_linearize
+    run = Runner(args.config, dev, args.symmetry_ignored)
+    s, nx = run.s, run.nx
+    # an L2 flush between steps (the workload inputs exceed L2 as well)
     flush = torch.empty(int(512 * 2 ** 20) // 4, dtype=torch.float32,
                         device="cuda")
     stream = torch.cuda.current_stream()
 
-    def options():
-        o = cdcc.cdcc_default_options()
-        o.device = dev
-        o.precision = {"fp64": cdcc.PREC_FP64, "mixed": cdcc.PREC_MIXED,
-                       "tc": cdcc.PREC_TC}[args.precision]
-        return o
-
-    def one(Lsrc, dLsrc, profile=False):
-        ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
-                                s.orb_irrep, s.eps, s.chol_irrep, Lsrc,
-                                options=options())
-        if profile:
-            cdcc.cdcc_profile(ctx, True)
-        e, g = cdcc.gradient(ctx, dLsrc)
-        stats = None
-        if profile:
-            stats = [cdcc.cdcc_kernel_stats(ctx, k) for k in range(6)]
-            stats.append(cdcc.cdcc_ladder_stats(ctx))
-        nl = cdcc.cdcc_kernel_launches(ctx)
-        ph = cdcc.cdcc_phase_times(ctx)
-        cdcc.cd_ccsd_free(ctx)
-        return e, g, nl, stats, ph
-
     for _ in range(args.warmup):
-        one(L_d, dL_d)
+        run.one(cdcc, args.precision, linearize=lin)
     torch.cuda.synchronize()
 
     # ---- device-resident timing (inputs in HBM), L2 flushed between steps
@@ -256,65 +423,91 @@ def run_ours(args, rank, ws):
     clk.start()
     barrier(ws)
     torch.cuda.synchronize()
-    times, launches = [], 0
-    agg = np.zeros((7, 3))
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        e, g, nl, stats, ph = one(L_d, dL_d, profile=True)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        times.append(ev0.elapsed_time(ev1) * 1e-3)
-        launches += nl
-        agg += np.array(stats)
+    times, infos, (e, g) = timed_steps(torch, run, cdcc, args.precision,
+                                       args.steps, flush, stream, lin)
     torch.cuda.synchronize()
     barrier(ws)
     clocks = clk.stop()
     t50 = allmax(float(np.median(times)), ws)
     t99 = allmax(float(np.percentile(times, 99)), ws)
+    classes, lad = class_table(infos, args.steps)
+    launches = int(np.mean([i["launches"] for i in infos]))
 
-    # ---- the other schedules on the same workload (mixed / TC vs FP64 GPU)
-    saved = args.precision
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = []
+    if args.e2e_steps > 0:
+        L_h, dL_h = run.host()
+        for _ in range(max(1, min(args.steps, args.e2e_steps))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            run.one(cdcc, args.precision, L_h.numpy(), dL_h.numpy(),
+                    linearize=lin)
+            e2e.append(time.perf_counter() - t0)
+    e2e50 = allmax(float(np.median(e2e)), ws) if e2e else None
+    h2d = (s.L.nbytes + run.dL.nbytes + s.eps.nbytes + s.orb_irrep.nbytes
+           + s.chol_irrep.nbytes)
+    d2h = 8 * (nx + 1)
+
+    # ---- other schedules on the same workload (optional)
     other_lines = []
     wanted = ("fp64", "mixed", "tc") if args.others == "all" else \
         tuple(x for x in args.others.split(",") if x and x != "none")
-    for other in [p for p in wanted if p != saved]:
-        args.precision = other
-        one(L_d, dL_d)                   # warm-up of the other schedule
-        o_times = []
-        for _ in range(max(1, min(args.steps, 3))):
-            flush.fill_(1.0)
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            o_e, o_g, _, o_stats, _ = one(L_d, dL_d, profile=True)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            o_times.append(ev0.elapsed_time(ev1) * 1e-3)
-        tc = o_stats[5]
-        lad = o_stats[6]
+    for other in [p for p in wanted if p != args.precision]:
+        run.one(cdcc, other, linearize=lin)
+        o_t, o_inf, (o_e, o_g) = timed_steps(torch, run, cdcc, other, 1,
+                                             flush, stream, lin)
+        ocls, olad = class_table(o_inf, 1)
         other_lines.append({
-            "precision": other,
-            "time_to_gradient_s": float(np.median(o_times)),
+            "precision": other, "time_to_gradient_s": o_t[0],
             "abs_dE_vs_this_run": abs(o_e - e),
             "max_abs_dg_vs_this_run": float(np.abs(o_g - g).max()),
-            "tc_gemm_s": tc[0],
-            "tc_gemm_tflops": tc[2] / tc[0] / 1e12 if tc[0] > 0 else None,
-            "ladder_s": lad[0],
-            "ladder_tflops": lad[1] / lad[0] / 1e12 if lad[0] > 0 else None})
-    args.precision = saved
+            "ladder_tflops": olad[1] / olad[0] / 1e12 if olad[0] else None})
+
+    # ---- mixed (this schedule) vs plain FP64 GPU path on the comparison
+    # workload, one gradient each after one warm-up of each
+    compare = None
+    if args.compare not in ("none", "") and args.precision != "fp64" \
+            and not args.symmetry_ignored:
+        cfg2 = int(args.compare)
+        r2 = run if cfg2 == args.config else Runner(cfg2, dev)
+        res = {}
+        for p in (args.precision, "fp64"):
+            if p != "fp64":
+                r2.one(cdcc, p, linearize=lin)   # warm-up (tile tuner, pools)
+            t, inf, (ee, gg) = timed_steps(torch, r2, cdcc, p, 1, flush,
+                                           stream, lin)
+            _, l2 = class_table(inf, 1)
+            res[p] = {"time_to_gradient_s": t[0], "e_corr": ee,
+                      "ladder_s": l2[0],
+                      "ladder_tflops": l2[1] / l2[0] / 1e12 if l2[0] else None,
+                      "iterations": inf[0]["solver"], "g": gg}
+        a, b = res[args.precision], res["fp64"]
+        compare = {
+            "workload": WORKLOAD[cfg2],
+            args.precision: {k: v for k, v in a.items() if k != "g"},
+            "fp64": {k: v for k, v in b.items() if k != "g"},
+            "speedup_vs_fp64": b["time_to_gradient_s"] / a["time_to_gradient_s"],
+            "abs_dE_vs_fp64": abs(a["e_corr"] - b["e_corr"]),
+            "max_abs_dg_vs_fp64": float(np.abs(a["g"] - b["g"]).max()),
+            "note": "the FP64 GPU path is not run on the D2h o=60 v=540 "
+                    "workload: at its c2 rate (DFMA-bound ladder, 9.6e12 + "
+                    "6.4e12 flop per application) it would take about half "
+                    "an hour per gradient"}
+        del r2
 
     # ---- error report of the --precision schedule (untimed)
     err_est = None
     if args.error_estimate:
+        o = cdcc.cdcc_default_options()
+        o.precision = prec_code(cdcc, args.precision)
+        o.ladder_linearize = 1 if lin else 0
         ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
-                                s.orb_irrep, s.eps, s.chol_irrep, L_d,
-                                options=options())
-        cdcc.gradient(ctx, dL_d)
+                                s.orb_irrep, s.eps, s.chol_irrep, run.L_d,
+                                options=o)
+        cdcc.gradient(ctx, run.dL_d)
         t0 = time.perf_counter()
-        dE, dg = cdcc.cdcc_error_estimate(ctx, dL_d)
+        dE, dg = cdcc.cdcc_error_estimate(ctx, run.dL_d)
         err_est = {"dE": dE, "max_dg": float(np.abs(dg).max()),
                    "seconds": time.perf_counter() - t0,
                    "what": "|E64(t)-E(t)| + |<lambda,R64(t)>| and "
@@ -322,72 +515,56 @@ def run_ours(args, rank, ws):
                            "converged t, lambda"}
         cdcc.cd_ccsd_free(ctx)
 
-    # ---- end to end through the C ABI with host buffers
-    e2e = []
-    for _ in range(max(0, min(args.steps, args.e2e_steps))):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        one(L_h.numpy(), dL_h.numpy())
-        e2e.append(time.perf_counter() - t0)
-    e2e50 = allmax(float(np.median(e2e)), ws) if e2e else None
-    h2d = (s.L.nbytes + dL.nbytes + s.eps.nbytes + s.orb_irrep.nbytes
-           + s.chol_irrep.nbytes)
-    d2h = 8 * (nx + 1)
-
     if rank != 0:
         return
-    # roofline of the dominant kernel class (FP64 GEMM) over the timed region
-    gsec, gn, gfl = agg[0]
-    achieved = gfl / gsec / 1e9 if gsec > 0 else 0.0
-    # ladder flops (algorithmic) per application, for the ladder TFLOP/s line
-    from synth.gen import packed_size  # noqa
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         try:
-            cpu = oracle_sample(args.config)
+            smp = OracleSample(args.config)
+            smp.time_blocks(1)               # warm-up, as in the reference arm
+            cpu = smp.estimate(1)
+            del smp
         except Exception as ex:  # pragma: no cover
             cpu = {"error": str(ex)}
-    classes = {}
-    for k, nm in enumerate(["gemm64", "permute", "update", "contract_dL",
-                            "other", "tc_gemm"]):
-        sec, n, w = agg[k]
-        classes[nm] = {"seconds": sec / args.steps, "launches": int(n /
-                                                                    args.steps),
-                       "work_per_step": w / args.steps}
+    roof = rooflines(classes, pk)
+    dom = max(roof, key=lambda k: roof[k]["seconds"]) if roof else None
+    roofline = dict(roof[dom], kernel=dom, traffic=None,
+                    traffic_note="no ncu DRAM capture of this kernel version "
+                                 "at this workload") if dom else None
+    info0 = infos[-1]
     out = {
         "metric": METRIC, "value": t50, "unit": "s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t50 * 1e3,
-        "p99_s": t99, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "p50_s": t50, "p99_s": t99, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": WORKLOAD[args.config] + (
                        " (C1 twin: irreps ignored)" if args.symmetry_ignored
                        else ""),
                    "precision": args.precision,
-                   "l2": "flushed between steps (512 MiB write)",
+                   "ladder_linearize": lin,
+                   "l2": "flushed between steps (512 MiB write); inputs "
+                         "larger than L2",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
         "e_corr": e, "gradients_per_s": ws / t50,
-        "gpu_launches": int(launches / args.steps),
-        "phases_s": {"ccsd": ph[0], "lambda": ph[1], "density": ph[2],
-                     "contract_dL": ph[3]},
+        "gpu_launches": launches,
+        "phases_s": dict(zip(["ccsd", "lambda", "density", "contract_dL"],
+                             info0["phases"])),
+        "iterations": dict(zip(["ccsd_bf16x3", "ccsd_accurate",
+                                "lambda_bf16x3", "lambda_accurate"],
+                               info0["solver"])),
         "peak_device_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
-        "error_estimate": err_est,
+        "ladder": {"seconds_per_step": lad[0], "flops_per_step": lad[1],
+                   "tflops": lad[1] / lad[0] / 1e12 if lad[0] > 0 else None,
+                   "share_of_step": lad[0] / t50,
+                   "note": "nominal flops of the ladder products, (ac|bd) "
+                           "builds from L^P_ab and their adjoints"},
         "kernel_classes": classes,
-        "ladder": {"seconds_per_step": agg[6][0] / args.steps,
-                   "flops_per_step": agg[6][1] / args.steps,
-                   "tflops": (agg[6][1] / agg[6][0] / 1e12
-                              if agg[6][0] > 0 else None),
-                   "share_of_step": agg[6][0] / args.steps / t50,
-                   "note": "algorithmic flops of the ladder products, "
-                           "(ac|bd) builds and their adjoints"},
-        "roofline": {"kernel": "gemm64_kernel (FP64 DFMA grouped GEMM)",
-                     "bound": "alu", "achieved": achieved / 1e3,
-                     "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_GFLOPS,
-                     "peak_source": "nominal GB300 FP64 from the profiling "
-                                    "recipe (not in MEASURED_PEAKS.json)",
-                     "traffic": None},
+        "roofline": roofline,
+        "rooflines": roof,
+        "mixed_vs_fp64": compare,
         "other_precisions": other_lines,
+        "error_estimate": err_est,
         "e2e": {"value": e2e50, "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clocks,
@@ -412,8 +589,7 @@ def run_serving(args, rank, ws):
     if rank == 0:
         cbuild.build()
     barrier(ws)
-    prec = {"fp64": cdcc.PREC_FP64, "mixed": cdcc.PREC_MIXED,
-            "tc": cdcc.PREC_TC}[args.precision]
+    prec = prec_code(cdcc, args.precision)
     specs = serving_jobs()[:args.jobs]
     reqs = []
     for sp in specs:
@@ -450,9 +626,7 @@ def run_serving(args, rank, ws):
         "value": p50, "unit": "s", "n_gpus": ws, "steps": 1,
         "warmup": max(1, args.warmup), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "bf16x3+f64",
-                  "tc": "bf16x3+exact-slice"}[args.precision],
-        "data": "synthetic",
+        "dtype": DTYPE[args.precision], "data": "synthetic",
         "config": {"workload": f"c4: {len(reqs)} requests, Poisson arrivals "
                                "mean 0.5 s, o~U{4..40}, v=9o, nL=40o, "
                                "C1/C2v/D2h, 2 displacements each",
@@ -470,15 +644,49 @@ def run_serving(args, rank, ws):
                       "admit_s": (r.t_admit - r.arrival
                                   if r.t_admit is not None else None),
                       "ladder": "stored" if r.ladder == cdcc.LADDER_STORED
-                      else "otf", "status": r.status, "e_corr": r.e}
+                      else "otf", "status": r.status, "e_corr": r.e,
+                      "error_dE": r.extra.get("dE")}
                      for r in reqs],
         "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
 
 
+def run_gemm(args):
+    """Time cdcc_dgemm (operand slicing included) on one product shape."""
+    import torch
+    from paper_2512_21909_gb300 import build as cbuild, cdcc
+    cbuild.build()
+    cdcc.load()
+    f = [int(x) for x in args.gemm.split(",")]
+    M, N, K = f[:3]
+    ta = f[3] if len(f) > 3 else 0
+    tb = f[4] if len(f) > 4 else 1
+    modes = [int(x) for x in args.gemm_modes.split(",")]
+    A = torch.randn((K, M) if ta else (M, K), dtype=torch.float64,
+                    device="cuda")
+    B = torch.randn((N, K) if tb else (K, N), dtype=torch.float64,
+                    device="cuda")
+    C = torch.zeros(M, N, dtype=torch.float64, device="cuda")
+    for mode in modes:
+        best = None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cdcc.cdcc_dgemm(ta, tb, M, N, K, 1.0, A, A.shape[1], B,
+                            B.shape[1], 0.0, C, N, mode=mode)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        print(f"M{M} N{N} K{K} ta{ta} tb{tb} mode{mode}: {best * 1e3:.2f} ms "
+              f"{2.0 * M * N * K / best / 1e12:.2f} TFLOP/s", flush=True)
+
+
 def main():
     args = parse()
+    if args.gemm:
+        run_gemm(args)
+        return
     rank, ws = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, ws)

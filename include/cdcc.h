@@ -114,6 +114,12 @@ typedef struct {
     int ladder;             /* cdcc_ladder (default CDCC_LADDER_AUTO)       */
     double ladder_batch_gb; /* OTF: GB of one (ab|cd) row batch (default 2) */
     int fock_model;         /* cdcc_fock_model (default CDCC_FIXED_CORE)    */
+    int ladder_linearize;   /* MIXED / TC accurate phase: the ladder (linear
+                               in its input) is evaluated accurately at an
+                               anchor and corrected in BF16x3 around it;
+                               convergence is accepted only on an iteration
+                               with a fresh accurate anchor (default 1;
+                               0 = every accurate iteration fully accurate) */
 } cdcc_options;
 
 typedef struct cdcc_ctx cdcc_ctx;
@@ -218,19 +224,23 @@ cdcc_status gradient(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
  * contraction as contract_dL for totally symmetric displacements, where
  * gamma is the packed Gamma^P_pq (see cdcc_get_gamma) and dL holds nx packed
  * derivative tensors back to back.
- *   gamma, dL, g  DEVICE pointers of the current device, owned by the caller
+ *   gamma, dL, g  DEVICE pointers of the current device (or managed
+ *                 memory), owned by the caller; host pointers and memory of
+ *                 another GPU return CDCC_EINVAL
  *   nx            1 .. CDCC_NOALLOC_MAX_NX, else CDCC_EINVAL
  *   nnz           elements per packed tensor (>= 1)
- *   stream        cudaStream_t (may be 0); the call only enqueues work, g is
- *                 valid once the stream reaches that point
+ *   stream        cudaStream_t of the current device (may be 0, a stream
+ *                 of another device returns CDCC_EINVAL); the call only
+ *                 enqueues work, g is valid once the stream reaches that point
  * No cudaMalloc / cudaFree or allocating library routine is called.  The
  * per-block partial sums live in a fixed device array of
- * 1216 x CDCC_NOALLOC_MAX_NX doubles (608 KiB) that every device loading the
- * library keeps until exit.  The first call on a device looks that array's
- * address up (with the device current), so make it before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * race on it and must be serialised.  Non-device pointers return
- * CDCC_EINVAL; a failed launch returns CDCC_ECUDA.
+ * 2048 x CDCC_NOALLOC_MAX_NX doubles (1 MiB) that every device loading the
+ * library keeps until exit; a call uses min(8 x SM count, 2048) blocks of it.
+ * The first call on a device looks that array's address up (with the device
+ * current), so make it before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU race on it and must be
+ * serialised.  A CUDA error already pending on the calling thread, or a
+ * failed launch, returns CDCC_ECUDA (a pending error is left in place).
  */
 #define CDCC_NOALLOC_MAX_NX 64
 cdcc_status cdcc_contract_dL_noalloc(const double *gamma, const double *dL,
@@ -253,7 +263,9 @@ cdcc_status cdcc_phase_times(cdcc_ctx *ctx, double *t4);
  * every launch of the class while enabled).  Classes:
  *   0 FP64 GEMM (work = flops)          1 permutation / axpy (work = bytes)
  *   2 amplitude update (work = bytes)   3 contract_dL batched dot (bytes)
- *   4 other vector kernels (bytes)     5 tensor-core GEMM (work = flops)
+ *   4 other vector kernels (bytes)      5 tensor-core GEMM, BF16 float
+ *   6 tensor-core GEMM, exact slices      slices (work = algorithmic
+ *     (work = algorithmic flops 2MNK)     flops 2MNK)
  * cdcc_kernel_stats returns the accumulated device seconds, launches and
  * algorithmic work since the context was created. */
 cdcc_status cdcc_profile(cdcc_ctx *ctx, int enable);
@@ -304,6 +316,133 @@ cdcc_status cdcc_dgemm(int transA, int transB, int M, int N, int K,
  * error.  The device stays usable afterwards.
  */
 cdcc_status cdcc_selftest_bounded_wait(void *stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop on one GPU that admits gradient jobs of mixed
+ * sizes and point groups as they arrive, by free slots and device memory,
+ * keeps each admitted job's state (amplitudes, Lambda, DIIS histories,
+ * intermediates) resident in its own context and runs the jobs concurrently
+ * on their own CUDA streams (continuous batching: a job that arrives while
+ * others run starts as soon as a slot and its memory are free).
+ *
+ * Admission: first come first served with a look-ahead of four jobs past
+ * the head of the queue; a job is admitted when a slot is free and its
+ * estimated peak device footprint (cdcc_job_footprint) fits the budget not
+ * yet promised to running jobs, or when nothing else runs.  A job whose
+ * device allocation fails anyway is put back at the head of the queue and
+ * retried when it can run alone (at most three retries).  The ladder mode
+ * of a job depends on its size only (stored when the stored integrals fit
+ * stored_max_gb), so a job's result does not depend on the jobs it ran
+ * beside.
+ * Threads: one dispatcher and max_active workers inside the library; the
+ * calls below may be made from any host thread.
+ */
+typedef struct cdcc_server cdcc_server;
+
+/* One gradient job.  Arrays as for cd_ccsd_init / contract_dL; host or
+ * device memory of the server's device; cdcc_submit copies them.        */
+typedef struct {
+    int nirrep, nocc, nvir, nchol;
+    const int32_t *orb_irrep;   /* [nocc+nvir]                           */
+    const double *eps;          /* [nocc+nvir]                           */
+    const int32_t *chol_irrep;  /* [nchol]                               */
+    const double *L;            /* packed L-pattern, G_x = 0             */
+    int nx;                     /* displacements (>= 0)                  */
+    const int32_t *x_irrep;     /* [nx] or NULL (all totally symmetric)  */
+    const double *dL;           /* the nx packed tensors, back to back   */
+} cdcc_job_desc;
+
+typedef enum {
+    CDCC_JOB_QUEUED = 0, CDCC_JOB_RUNNING = 1, CDCC_JOB_DONE = 2,
+    CDCC_JOB_FAILED = 3
+} cdcc_job_state;
+
+typedef struct {
+    int state;            /* cdcc_job_state                               */
+    int status;           /* cdcc_status of a finished job (DONE: OK)     */
+    int nx;               /* displacements of the job                     */
+    int ladder;           /* ladder mode the job ran with                 */
+    int retries;          /* allocation failures retried                  */
+    double e_corr;        /* correlation energy (DONE)                    */
+    double err_dE;        /* error report of e_corr (DONE; see
+                             cdcc_energy_error)                           */
+    double t_wait;        /* seconds from submission to admission         */
+    double t_run;         /* seconds from admission to completion         */
+    double *g;            /* in: caller buffer of >= nx doubles or NULL;
+                             the gradient is written there once DONE      */
+    char message[160];    /* reason of a FAILED job                       */
+} cdcc_result;
+
+/* Host-side stand-in for the gradient of a job (tests of the scheduling
+ * logic without a GPU, or embedding a different executor): fills *e_corr,
+ * g[nx], *err_dE and returns a cdcc_status (CDCC_ENOMEM = allocation failed,
+ * the job is retried).                                                    */
+typedef int (*cdcc_executor_fn)(uint64_t ticket, const cdcc_job_desc *job,
+                                int slot, double *e_corr, double *g,
+                                double *err_dE, void *user);
+
+typedef struct {
+    int max_active;         /* slots: jobs in flight (default 4)           */
+    double budget_gb;       /* device memory the jobs may use; 0 = the free
+                               memory at creation minus reserve_gb          */
+    double reserve_gb;      /* kept free when budget_gb = 0 (default 8)    */
+    double stored_max_gb;   /* stored ladder when its integrals need at most
+                               this much (default 24), else on the fly     */
+    int error_report;       /* attach cdcc_energy_error to every result
+                               (default 1)                                  */
+    cdcc_executor_fn executor;  /* NULL = the library's gradient          */
+    void *executor_user;
+} cdcc_server_options;
+
+void cdcc_server_default_options(cdcc_server_options *sopt);
+
+/* Create a server on opt->device (opt: options of every job; NULL =
+ * defaults; its stream, allocator and ladder fields are ignored: every slot
+ * has its own stream and jobs allocate with cudaMallocAsync on it).       */
+cdcc_status cdcc_server_create(cdcc_server **out, const cdcc_options *opt,
+                               const cdcc_server_options *sopt);
+
+/* Queue a job (inputs copied before returning); *ticket identifies it.
+ * CDCC_EINVAL for inconsistent sizes, CDCC_ESTATE after shutdown began.   */
+cdcc_status cdcc_submit(cdcc_server *srv, const cdcc_job_desc *job,
+                        uint64_t *ticket);
+
+/* Non-blocking state of a job; res->g (if set) receives the gradient once
+ * the job is DONE.  CDCC_EINVAL for an unknown ticket.                    */
+cdcc_status cdcc_poll(cdcc_server *srv, uint64_t ticket, cdcc_result *res);
+
+/* Block until the job finishes or timeout_s passes (then CDCC_ETIMEOUT),
+ * then as cdcc_poll.                                                      */
+cdcc_status cdcc_wait(cdcc_server *srv, uint64_t ticket, double timeout_s,
+                      cdcc_result *res);
+
+/* Largest number of jobs that ran at once so far.                         */
+int cdcc_server_max_active_seen(const cdcc_server *srv);
+
+/* Estimated peak device bytes of a job with the given precision and ladder
+ * mode (the admission estimate; on-the-fly batches of batch_gb).          */
+size_t cdcc_job_footprint(const cdcc_job_desc *job, int precision,
+                          int ladder, double batch_gb);
+
+/* Stop accepting jobs, let running jobs finish, fail queued ones, free. */
+void cdcc_server_destroy(cdcc_server *srv);
+
+/*
+ * Error report of the correlation energy (Sec. 2 precision schedule; cheap
+ * enough to attach to every result): what the accurate arithmetic of the
+ * schedule leaves in E_corr.
+ *   CDCC_PREC_TC     the exact-slice arithmetic with s = 4 slices keeps 7
+ *                    more bits per operand than s = 3; one residual with
+ *                    s = 3 at the converged amplitudes t gives
+ *                      dE_3 = |E_3(t) - E_4(t)| + |<lambda, R_3(t) - R_4(t)>|
+ *                    and the report is dE_3 / 2^7 plus the convergence
+ *                    term |<lambda, R_4(t)>|;
+ *   FP64 / MIXED     the convergence term |<lambda, R(t)>| (FP64 rounding is
+ *                    far below it).
+ * Requires lambda_solve.  Cost: one residual in the 3-slice arithmetic (TC)
+ * or none.  The recorded intermediates are re-evaluated when next needed.
+ */
+cdcc_status cdcc_energy_error(cdcc_ctx *ctx, double *dE);
 
 /* Number of kernels this context has launched so far. */
 long long cdcc_kernel_launches(const cdcc_ctx *ctx);

@@ -40,7 +40,8 @@ class cdcc_options(ctypes.Structure):
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_user", ctypes.c_void_p), ("ladder", ctypes.c_int),
                 ("ladder_batch_gb", ctypes.c_double),
-                ("fock_model", ctypes.c_int)]
+                ("fock_model", ctypes.c_int),
+                ("ladder_linearize", ctypes.c_int)]
 
 
 class CdccError(RuntimeError):
@@ -318,7 +319,7 @@ def cdcc_phase_times(ctx):
 
 
 KERNEL_CLASSES = ("gemm64", "permute", "update", "contract_dL", "other",
-                  "tc_gemm")
+                  "tc_float_slices", "tc_exact_slices")
 
 
 def cdcc_solver_info(ctx):
@@ -439,3 +440,168 @@ def init_from_system(sysm, **kw) -> Context:
     """cd_ccsd_init from a synth.System (host arrays)."""
     return cd_ccsd_init(sysm.nirrep, sysm.nocc, sysm.nvir, sysm.nchol,
                         sysm.orb_irrep, sysm.eps, sysm.chol_irrep, sysm.L, **kw)
+
+
+# ------------------------------------------------------------------ serving
+class cdcc_job_desc(ctypes.Structure):
+    _fields_ = [("nirrep", ctypes.c_int), ("nocc", ctypes.c_int),
+                ("nvir", ctypes.c_int), ("nchol", ctypes.c_int),
+                ("orb_irrep", ctypes.c_void_p), ("eps", ctypes.c_void_p),
+                ("chol_irrep", ctypes.c_void_p), ("L", ctypes.c_void_p),
+                ("nx", ctypes.c_int), ("x_irrep", ctypes.c_void_p),
+                ("dL", ctypes.c_void_p)]
+
+
+class cdcc_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ladder", ctypes.c_int),
+                ("retries", ctypes.c_int), ("e_corr", ctypes.c_double),
+                ("err_dE", ctypes.c_double), ("t_wait", ctypes.c_double),
+                ("t_run", ctypes.c_double), ("g", ctypes.c_void_p),
+                ("message", ctypes.c_char * 160)]
+
+
+EXECUTOR_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_uint64,
+                               ctypes.POINTER(cdcc_job_desc), ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_void_p)
+
+
+class cdcc_server_options(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("budget_gb", ctypes.c_double),
+                ("reserve_gb", ctypes.c_double),
+                ("stored_max_gb", ctypes.c_double),
+                ("error_report", ctypes.c_int), ("executor", EXECUTOR_FN),
+                ("executor_user", ctypes.c_void_p)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = range(4)
+
+
+def _server_lib():
+    lib = load()
+    if not hasattr(lib, "_server_typed"):
+        P = ctypes.POINTER
+        vp = ctypes.c_void_p
+        lib.cdcc_server_default_options.argtypes = [P(cdcc_server_options)]
+        lib.cdcc_server_default_options.restype = None
+        lib.cdcc_server_create.argtypes = [P(vp), P(cdcc_options),
+                                           P(cdcc_server_options)]
+        lib.cdcc_server_create.restype = ctypes.c_int
+        lib.cdcc_submit.argtypes = [vp, P(cdcc_job_desc),
+                                    P(ctypes.c_uint64)]
+        lib.cdcc_submit.restype = ctypes.c_int
+        lib.cdcc_poll.argtypes = [vp, ctypes.c_uint64, P(cdcc_result)]
+        lib.cdcc_poll.restype = ctypes.c_int
+        lib.cdcc_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double,
+                                  P(cdcc_result)]
+        lib.cdcc_wait.restype = ctypes.c_int
+        lib.cdcc_server_max_active_seen.argtypes = [vp]
+        lib.cdcc_server_max_active_seen.restype = ctypes.c_int
+        lib.cdcc_job_footprint.argtypes = [P(cdcc_job_desc), ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_double]
+        lib.cdcc_job_footprint.restype = ctypes.c_size_t
+        lib.cdcc_server_destroy.argtypes = [vp]
+        lib.cdcc_server_destroy.restype = None
+        lib.cdcc_energy_error.argtypes = [vp, P(ctypes.c_double)]
+        lib.cdcc_energy_error.restype = ctypes.c_int
+        lib._server_typed = True
+    return lib
+
+
+def cdcc_server_default_options() -> cdcc_server_options:
+    o = cdcc_server_options()
+    _server_lib().cdcc_server_default_options(ctypes.byref(o))
+    return o
+
+
+def job_desc(nirrep, nocc, nvir, nchol, orb_irrep, eps, chol_irrep, L, dL,
+             x_irrep=None):
+    """(cdcc_job_desc, keepalive) for host arrays (numpy)."""
+    oi, ci = _i32(orb_irrep), _i32(chol_irrep)
+    e, Lh = _f64(eps), _f64(L)
+    dLh = _f64(dL)
+    nx = int(dLh.shape[0]) if dLh.ndim > 1 else (1 if dLh.size else 0)
+    xi = _i32(x_irrep) if x_irrep is not None else None
+    d = cdcc_job_desc(int(nirrep), int(nocc), int(nvir), int(nchol),
+                      oi.ctypes.data, e.ctypes.data, ci.ctypes.data,
+                      Lh.ctypes.data, nx,
+                      xi.ctypes.data if xi is not None else None,
+                      dLh.ctypes.data if dLh.size else None)
+    return d, (oi, ci, e, Lh, dLh, xi)
+
+
+def cdcc_job_footprint(desc, precision, ladder, batch_gb=2.0) -> int:
+    return int(_server_lib().cdcc_job_footprint(ctypes.byref(desc),
+                                                int(precision), int(ladder),
+                                                float(batch_gb)))
+
+
+def cdcc_energy_error(ctx) -> float:
+    """Error report of E_corr (see include/cdcc.h)."""
+    dE = ctypes.c_double()
+    _check(ctx, _server_lib().cdcc_energy_error(ctx.handle,
+                                                ctypes.byref(dE)))
+    return dE.value
+
+
+class Server:
+    """Owns a cdcc_server* (include/cdcc.h serving entry points)."""
+
+    def __init__(self, options: cdcc_options | None = None,
+                 server_options: cdcc_server_options | None = None):
+        lib = _server_lib()
+        self.opt = options if options is not None else cdcc_default_options()
+        self.sopt = (server_options if server_options is not None
+                     else cdcc_server_default_options())
+        self.handle = ctypes.c_void_p()
+        self._keep = {}
+        st = lib.cdcc_server_create(ctypes.byref(self.handle),
+                                    ctypes.byref(self.opt),
+                                    ctypes.byref(self.sopt))
+        if st != CDCC_OK:
+            raise CdccError(st, "cdcc_server_create failed")
+
+    def submit(self, desc, keep) -> int:
+        t = ctypes.c_uint64()
+        st = _server_lib().cdcc_submit(self.handle, ctypes.byref(desc),
+                                       ctypes.byref(t))
+        if st != CDCC_OK:
+            raise CdccError(st, "cdcc_submit failed")
+        return int(t.value)
+
+    def poll(self, ticket, nx):
+        g = np.zeros(max(nx, 1))
+        r = cdcc_result()
+        r.g = g.ctypes.data
+        st = _server_lib().cdcc_poll(self.handle, ctypes.c_uint64(ticket),
+                                     ctypes.byref(r))
+        if st != CDCC_OK:
+            raise CdccError(st, "cdcc_poll failed")
+        return r, g[:nx]
+
+    def wait(self, ticket, nx, timeout_s=-1.0):
+        g = np.zeros(max(nx, 1))
+        r = cdcc_result()
+        r.g = g.ctypes.data
+        st = _server_lib().cdcc_wait(self.handle, ctypes.c_uint64(ticket),
+                                     float(timeout_s), ctypes.byref(r))
+        if st not in (CDCC_OK, CDCC_ETIMEOUT):
+            raise CdccError(st, "cdcc_wait failed")
+        return r, g[:nx]
+
+    def max_active_seen(self) -> int:
+        return int(_server_lib().cdcc_server_max_active_seen(self.handle))
+
+    def close(self):
+        if self.handle:
+            _server_lib().cdcc_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -118,6 +118,12 @@ struct cdcc_ctx {
   std::string err;
   int state = 0;  // 1 init, 2 ccsd, 3 lambda, 4 density
   bool tape_ready = false;
+  // the engine's intermediates hold an accurate residual evaluation at the
+  // current amplitudes (set when CCSD converges), so recording the tape
+  // needs no second evaluation
+  bool fwd_fresh = false;
+  // c->res holds the accurate residual at the converged amplitudes
+  bool res_acc = false;
   double e_corr = 0, e_ref = 0;
   int64_t nnz0 = 0;
   double* d_eps = nullptr;
@@ -298,7 +304,7 @@ void residual(cdcc_ctx* c) {
   if (c->otf)
     e.ladder(1.0, t2s, c->Lvv, Rr);                              // PPL
   else
-    e.contract(1.0, t2s, "ijcd", c->W0, "abcd", 1.0, Rr, "ijab"); // PPL
+    e.ladder_stored(1.0, t2s, c->W0, Rr);                        // PPL
   Tensor* Yl = T("Ylad", {SO, SO, SO, SV}, 2);
   e.contract(1.0, t2s, "ijcd", c->Govvv, "mcbd", 0.0, Yl, "ijmb");
   e.contract(-1.0, T1, "ma", Yl, "ijmb", 1.0, Rr, "ijab");
@@ -524,9 +530,21 @@ void check_device_error(cdcc_ctx* c) {
                           std::to_string(err) + ")");
 }
 
+// Linearised ladder in the accurate phase (MIXED and TC schedules, see
+// Engine::ladder_lin): the anchor is evaluated accurately when the phase
+// starts, later iterations correct it in BF16x3, and convergence is only
+// accepted on an iteration whose ladder was a fresh accurate anchor, so the
+// converged amplitudes solve the accurate equations.
+bool linearised(cdcc_ctx* c) {
+  return mixed(c) && c->opt.ladder_linearize != 0;
+}
+
 void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 0);
+  c->fwd_fresh = false;
+  c->res_acc = false;
+  e.ladder_lin(0, 0);
   e.zero(c->amp);
   // the amplitude-independent integrals enter every later FP64 iteration, so
   // they are built with FP64-accurate products
@@ -549,11 +567,17 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
     if (!std::isfinite(rmax) || !std::isfinite(E))
       throw StatusError(CDCC_ENUMERIC, "non-finite CCSD residual");
     if (!early && rmax <= c->opt.conv_tol && have_old &&
-        std::fabs(E - e_old) <= c->opt.energy_tol)
-      break;
+        std::fabs(E - e_old) <= c->opt.energy_tol) {
+      if (!linearised(c) || e.ladder_lin_anchored(0)) break;
+      // converged around an older anchor: re-evaluate at the same
+      // amplitudes with a fresh accurate anchor before accepting
+      e.ladder_lin(0, 1);
+      continue;
+    }
     if (early && sw.done(rmax)) {
       early = false;        // re-evaluate at the same amplitudes, accurately
       e.set_precision(exact_prec(c));
+      if (linearised(c)) e.ladder_lin(0, 1);
       have_old = false;
       continue;
     }
@@ -564,10 +588,15 @@ void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
     });
     if (it >= 2) diis_step(c, c->cc_diis, c->amp, c->err1);
   }
+  e.ladder_lin(0, 0);
   pt.stop();
   check_device_error(c);
   if (it > c->opt.max_iter)
     throw StatusError(CDCC_ENOCONV, "CCSD did not converge");
+  // the last evaluation was accurate (and its ladder a fresh anchor) at the
+  // converged amplitudes: the tape can be recorded without re-running it
+  c->fwd_fresh = true;
+  c->res_acc = true;
   c->e_corr = E - c->e_ref;
   if (e_corr) *e_corr = c->e_corr;
   if (iters) *iters = it;
@@ -582,11 +611,18 @@ void ensure_tape(cdcc_ctx* c) {
   e.record(true);
   e.record_only(true);   // the t-independent integrals are already built
   prepare(c);
-  e.record_only(false);
-  const int prec = e.precision();
-  e.set_precision(exact_prec(c));
-  residual(c);
-  e.set_precision(prec);
+  if (c->fwd_fresh) {
+    // the intermediates of the last (accurate) CCSD evaluation are those
+    // at the current amplitudes: record the residual without executing it
+    residual(c);
+    e.record_only(false);
+  } else {
+    e.record_only(false);
+    const int prec = e.precision();
+    e.set_precision(exact_prec(c));
+    residual(c);
+    e.set_precision(prec);
+  }
   e.record(false);
   c->tape_ready = true;
 }
@@ -604,6 +640,7 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
   diis_init(c, c->lam_diis, "ccdiis", c->lam->lay.size);
   Tensor* g1 = e.adjoint(c->T1);
   Tensor* g2 = e.adjoint(c->T2);
+  e.ladder_lin(1, 0);
   double rmax = 0;
   int it = 1;
   for (; it <= c->opt.max_iter; ++it) {
@@ -612,10 +649,15 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
     rmax = probe_step(c, g1, g2, c->err1);
     if (!std::isfinite(rmax))
       throw StatusError(CDCC_ENUMERIC, "non-finite Lambda residual");
-    if (!early && rmax <= c->opt.conv_tol) break;
+    if (!early && rmax <= c->opt.conv_tol) {
+      if (!linearised(c) || e.ladder_lin_anchored(1)) break;
+      e.ladder_lin(1, 1);   // accept only on a fresh accurate anchor
+      continue;
+    }
     if (early && sw.done(rmax)) {
       early = false;
       e.set_precision(exact_prec(c));
+      if (linearised(c)) e.ladder_lin(1, 1);
       continue;
     }
     e.timed(Engine::K_OTHER, 24.0 * c->lam->lay.size, [&] {
@@ -623,6 +665,7 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
     });
     if (it >= 2) diis_step(c, c->lam_diis, c->lam, c->err1);
   }
+  e.ladder_lin(1, 0);
   pt.stop();
   check_device_error(c);
   if (it > c->opt.max_iter)
@@ -820,6 +863,7 @@ void run_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   const int prec = e.precision();
   e.set_precision(0);
   residual(c);                       // FP64 E, R and tape intermediates at t
+  c->res_acc = false;
   const double E64 = scalar(c, c->E) - c->e_ref;
   const double* lam = c->lam->d;
   e.timed(Engine::K_OTHER, 16.0 * c->lam->lay.size, [&] {
@@ -843,6 +887,53 @@ void run_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   CK(cudaStreamSynchronize(c->st));
   e.set_precision(prec);
   check_device_error(c);
+}
+
+double lam_dot_res(cdcc_ctx* c) {
+  Engine& e = *c->eng;
+  const double* lam = c->lam->d;
+  e.timed(Engine::K_OTHER, 16.0 * c->lam->lay.size, [&] {
+    return multi_dot(&lam, 1, c->res->d, c->lam->lay.size, c->d_partial,
+                     c->d_dots, c->st);
+  });
+  double v = 0;
+  CK(cudaMemcpyAsync(&v, c->d_dots, 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return v;
+}
+
+// Error report of E_corr (cdcc_energy_error): the convergence term
+// <lambda, R(t)> and, for the exact-slice schedule, the change of the energy
+// functional E + <lambda, R> between 3 and 4 exact slices, divided by 2^7
+// (each slice keeps 7 more bits of every operand).
+void run_energy_error(cdcc_ctx* c, double* dE) {
+  Engine& e = *c->eng;
+  if (!c->res_acc) {
+    // the accurate residual at t is needed again
+    const int prec = e.precision();
+    e.set_precision(exact_prec(c));
+    residual(c);
+    e.set_precision(prec);
+    c->res_acc = true;
+  }
+  const double conv = lam_dot_res(c);
+  double out = std::fabs(conv);
+  if (c->opt.precision == CDCC_PREC_TC) {
+    const double E4 = c->e_corr + c->e_ref;
+    const int prec = e.precision();
+    e.set_precision(13);
+    residual(c);
+    e.set_precision(prec);
+    const double E3 = scalar(c, c->E);
+    const double conv3 = lam_dot_res(c);
+    out += (std::fabs(E3 - E4) + std::fabs(conv3 - conv)) / 128.0;
+    // c->res and the recorded intermediates now hold the 3-slice values
+    c->res_acc = false;
+    c->fwd_fresh = false;
+    c->tape_ready = false;
+  }
+  check_device_error(c);
+  *dE = out;
 }
 
 void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
@@ -1128,6 +1219,7 @@ void cdcc_default_options(cdcc_options* o) {
   o->ladder = CDCC_LADDER_AUTO;
   o->ladder_batch_gb = 2.0;
   o->fock_model = CDCC_FIXED_CORE;
+  o->ladder_linearize = 1;
 }
 
 cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
@@ -1216,6 +1308,15 @@ cdcc_status cdcc_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   }
   if (nx < 0 || (nx > 0 && (!dL || !dg))) return CDCC_EINVAL;
   return guarded(c, [&] { run_error_estimate(c, nx, x_irrep, dL, dE, dg); });
+}
+
+cdcc_status cdcc_energy_error(cdcc_ctx* c, double* dE) {
+  if (!c || !dE) return CDCC_EINVAL;
+  if (c->state < 3) {
+    c->err = "cdcc_energy_error before lambda_solve";
+    return CDCC_ESTATE;
+  }
+  return guarded(c, [&] { run_energy_error(c, dE); });
 }
 
 cdcc_status gradient(cdcc_ctx* c, int nx, const int32_t* x_irrep,

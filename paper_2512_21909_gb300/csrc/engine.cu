@@ -331,7 +331,7 @@ const DevTasks& Engine::perm_tasks(const Layout& Y, const Layout& X,
   int64_t total = 0;
   for (const PermTask& t : tasks) total += t.n;
   int CH = chunk_elems();
-  while (CH > 512 && total / CH < 4 * 152) CH /= 2;
+  while (CH > 512 && total / CH < 4 * (int64_t)sm_count()) CH /= 2;
   for (int i = 0; i < (int)tasks.size(); ++i)
     for (int64_t s = 0; s < tasks[i].n; s += CH)
       chunks.push_back({i, (int)std::min<int64_t>(CH, tasks[i].n - s), s});
@@ -360,7 +360,8 @@ const DevTasks& Engine::update_tasks(const Layout& L) {
 
 void Engine::axpy_raw(double alpha, const Layout& XL, const double* X,
                       const std::string& ix, double beta, const Layout& YL,
-                      double* Y, const std::string& iy) {
+                      double* Y, const std::string& iy,
+                      const double* d_scale) {
   if ((int)ix.size() != XL.rank || (int)iy.size() != YL.rank ||
       XL.rank != YL.rank)
     throw EngineError("axpy: rank / index string mismatch " + ix + "->" + iy);
@@ -381,7 +382,8 @@ void Engine::axpy_raw(double alpha, const Layout& XL, const double* X,
     nel = (beta == 0.0 ? 16 : 24) * (dt.embed ? XL.size : YL.size);
   }
   timed(K_PERM, (double)nel, [&] {
-    return perm_axpy(dt.tasks, dt.chunks, dt.nchunk, alpha, X, beta, Y, st_);
+    return perm_axpy(dt.tasks, dt.chunks, dt.nchunk, alpha, X, beta, Y, st_,
+                     d_scale);
   });
 }
 
@@ -408,6 +410,25 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   if (prof_on_) {
     tr_a = get_event();
     cudaEventRecord(tr_a, st_);
+  }
+  // one operand a scalar (no summed index, e.g. the adjoint of an energy
+  // contraction): C = beta*C + alpha*s*perm(other), a scaled permutation
+  // read from the device scalar s instead of a GEMM with K = 1
+  if ((A->lay.rank == 0 || B->lay.rank == 0) && A->lay.rank + B->lay.rank ==
+                                                     C->lay.rank) {
+    Tensor* S = A->lay.rank == 0 ? A : B;
+    Tensor* X = A->lay.rank == 0 ? B : A;
+    const std::string& ix = A->lay.rank == 0 ? ib : ia;
+    if (S->lay.gtot == 0 && S->lay.size == 1 && X->lay.gtot == C->lay.gtot) {
+      axpy_raw(alpha, X->lay, X->d, ix, beta, C->lay, C->d, ic, S->d);
+      if (tr_a) {
+        cudaEvent_t tr_b = get_event();
+        cudaEventRecord(tr_b, st_);
+        trace_pending_.push_back(
+            {ia + ',' + ib + "->" + ic + " [scaled axpy]", tr_a, tr_b, 0.0});
+      }
+      return;
+    }
   }
 
   std::string KA, KB, fA_A, fB_B, fA_C, fB_C;
@@ -609,8 +630,10 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
 
 // Route the blocks of one product (they write disjoint parts of C) to the
 // tensor cores or the FP64 kernel and launch them.  Tensor cores only take
-// matrix-shaped blocks: thin products (dots, outer products, o x o results)
-// stay on the FP64 path with split K.  Returns the path taken.
+// matrix-shaped blocks (both output sides >= 32, K >= 32; K is padded to the
+// 64-wide slice rows): thin products (dots, outer products, o x o results,
+// sums over one occupied index) stay on the FP64 path with split K.  Returns
+// the path taken.
 const char* Engine::run_gemms(const GemmProb* probs, int np, const Mat& mp,
                               const Mat& mq, double alpha, double beta) {
   double fl = 0;
@@ -621,10 +644,11 @@ const char* Engine::run_gemms(const GemmProb* probs, int np, const Mat& mp,
   GemmProb ptc[GEMM_MAXPROB], p64[GEMM_MAXPROB];
   int ntc = 0, n64 = 0;
   double fl_tc = 0;
+  const int prec = active_precision();
   for (int i = 0; i < np; ++i) {
     const GemmProb& g = probs[i];
-    if (tc_slices_ > 0 && std::min(g.M, g.N) >= 32 &&
-        std::max(g.M, g.N) >= 64 && g.K >= 128) {
+    if (prec > 0 && std::min(g.M, g.N) >= 32 &&
+        std::max(g.M, g.N) >= 64 && g.K >= 32) {
       fl_tc += 2.0 * g.M * (double)g.N * g.K;
       ptc[ntc++] = g;
     } else {
@@ -637,8 +661,8 @@ const char* Engine::run_gemms(const GemmProb* probs, int np, const Mat& mp,
     fl_tc = 0;
   }
   const char* path = ntc == 0 ? "fp64" : n64 == 0
-                         ? (tc_slices_ >= 12 ? "exact" : "split")
-                         : (tc_slices_ >= 12 ? "exact+fp64" : "split+fp64");
+                         ? (prec >= 12 ? "exact" : "split")
+                         : (prec >= 12 ? "exact+fp64" : "split+fp64");
   if (ntc > 0) tc_contract(ptc, ntc, mp, mq, alpha, beta, fl_tc);
   if (n64 > 0) {
     const double f64 = fl - fl_tc;
@@ -735,8 +759,9 @@ SlicedOp Engine::slice_side(Tensor* src, const double* ptr, int rows, int K,
 // launch of the split-precision (1-3 slices) or exact-slice (12-14) kernel.
 void Engine::tc_contract(const GemmProb* probs, int np, const Mat& mp,
                          const Mat& mq, double alpha, double beta, double fl) {
-  const bool exact = tc_slices_ >= 12;
-  const int ns = exact ? tc_slices_ - 10 : tc_slices_;
+  const int prec = active_precision();
+  const bool exact = prec >= 12;
+  const int ns = exact ? prec - 10 : prec;
   int64_t wsb = 1024;
   for (int i = 0; i < np; ++i) {
     const int64_t Kp = slice_kp(probs[i].K);
@@ -763,7 +788,7 @@ void Engine::tc_contract(const GemmProb* probs, int np, const Mat& mp,
   }
   tc_flops += (int64_t)fl;
   if (exact) {
-    timed(K_TC, fl, [&] {
+    timed(K_OZ, fl, [&] {
       return oz_gemm_sliced(tp, np, alpha, beta, ns, d_err, st_);
     });
   } else {
@@ -816,9 +841,19 @@ void Engine::backward(const std::vector<std::pair<Tensor*, Tensor*>>& seeds,
         contract(op.alpha, op.A, op.ia.c_str(), Cb, op.ic.c_str(), 1.0,
                  adjoint(op.B), op.ib.c_str());
     } else if (op.kind == 2) {
-      ladder_adjoint(op.alpha, Cb, op.A, op.B,
-                     op.A->req ? adjoint(op.A) : nullptr,
-                     op.B->req ? adjoint(op.B) : nullptr);
+      if (op.A->req && !op.B->req)   // amplitude adjoint only: the same map
+        ladder_lin_apply(1, op.alpha, Cb, op.B, false, adjoint(op.A));
+      else
+        ladder_adjoint(op.alpha, Cb, op.A, op.B,
+                       op.A->req ? adjoint(op.A) : nullptr,
+                       op.B->req ? adjoint(op.B) : nullptr);
+    } else if (op.kind == 3) {
+      // R[ij,ab] += alpha T[ij,cd] W[ab,cd]; W symmetric per block
+      if (op.A->req)
+        ladder_lin_apply(1, op.alpha, Cb, op.B, true, adjoint(op.A));
+      if (op.B->req)
+        contract(op.alpha, op.A, "ijcd", Cb, "ijab", 1.0, adjoint(op.B),
+                 "abcd");
     } else {
       if (op.A->req)
         axpy(op.alpha, Cb, op.ic.c_str(), 1.0, adjoint(op.A), op.ia.c_str());

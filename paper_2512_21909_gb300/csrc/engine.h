@@ -107,8 +107,28 @@ class Engine {
   // (ab|cd) order and applied at once.  Recorded as one tape operation whose
   // adjoint rebuilds the batches (T and L adjoints).
   void ladder(double alpha, Tensor* T, Tensor* L, Tensor* R);
+  // The same ladder with the (ac|bd) integrals stored as W[(ab),(cd)]
+  // (symmetric per block):  R[ij,ab] += alpha * sum_cd T[ij,cd] W[ab,cd].
+  // Recorded as one tape operation (adjoints for T and W).
+  void ladder_stored(double alpha, Tensor* T, Tensor* W, Tensor* R);
   // device bytes of one row batch of the (ab|cd) matrix (two such buffers)
   int64_t ladder_batch_bytes = (int64_t)2 << 30;
+
+  // Linearised ladder for the accurate phase of the mixed schedules.  The
+  // ladder is linear in its input X (the amplitudes in the forward
+  // residual, the adjoint dR in the Lambda sweep; W symmetric makes both the
+  // same map Lad).  With an anchor X0 evaluated in the accurate arithmetic,
+  //     Lad(X) = Lad_acc(X0) + Lad_delta(X - X0),
+  // where Lad_delta runs in the cheaper arithmetic `prec`; its rounding
+  // error scales with |X - X0|, which is small once the iterations are near
+  // convergence.  which = 0: forward ladder, 1: amplitude adjoint of the
+  // ladder (used when the Cholesky vectors need no adjoint).  mode 0: off
+  // (every call accurate), 1: the next call evaluates a new anchor
+  // accurately (then mode 2), 2: apply around the anchor.
+  void ladder_lin(int which, int mode, int prec = 2);
+  // true when the last linearised call of `which` evaluated an anchor (its
+  // result was then the accurate ladder)
+  bool ladder_lin_anchored(int which) const { return lin_[which].anchored; }
 
   // tape
   void record(bool on) { recording_ = on; }
@@ -139,13 +159,18 @@ class Engine {
   // (a change drops the cached slices of the previous arithmetic)
   void set_precision(int slices);
   int precision() const { return tc_slices_; }
+  // arithmetic in effect for the next contraction (a temporary override of
+  // the linearised ladder, else the precision set above)
+  int active_precision() const {
+    return tc_override_ >= 0 ? tc_override_ : tc_slices_;
+  }
   int64_t tc_min_flops = (int64_t)1 << 26;
   unsigned int* d_err = nullptr;   // device error flag of bounded waits
   int64_t tc_flops = 0;            // algorithmic flops run on tensor cores
 
   // Optional per-kernel-class timing with CUDA events on the engine stream.
   enum ProfKind : int { K_GEMM64 = 0, K_PERM = 1, K_UPDATE = 2, K_DOT = 3,
-                        K_OTHER = 4, K_TC = 5, K_NKIND = 6 };
+                        K_OTHER = 4, K_TC = 5, K_OZ = 6, K_NKIND = 7 };
   void profile(bool on) { prof_on_ = on; }
   template <class F>
   void timed(int kind, double work, F launch) {
@@ -174,7 +199,8 @@ class Engine {
 
  private:
   struct Op {
-    int kind;  // 0 contract, 1 axpy, 2 ladder (A = T, B = L, C = R)
+    int kind;  // 0 contract, 1 axpy, 2 ladder (A = T, B = L, C = R),
+               // 3 stored ladder (A = T, B = W, C = R)
     double alpha, beta;
     Tensor *A, *B, *C;
     std::string ia, ib, ic;
@@ -228,6 +254,18 @@ class Engine {
   void ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
                       Tensor* dT, Tensor* dL);
   void ladder_reserve(int64_t n);
+  // plain ladder map Y += alpha * Lad(X) (on the fly from L, or stored W)
+  void ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
+                  Tensor* Y);
+  struct LadderLin {
+    int mode = 0, prec = 2;
+    bool anchored = false;
+    Tensor *in = nullptr, *out = nullptr, *d = nullptr;
+  };
+  LadderLin lin_[2];
+  void ladder_lin_apply(int which, double alpha, Tensor* X, Tensor* LW,
+                        bool stored, Tensor* Y);
+  int tc_override_ = -1;
   double* lad_x_ = nullptr;
   double* lad_w_ = nullptr;
   int64_t lad_n_ = 0;
@@ -238,7 +276,8 @@ class Engine {
                              const int* xq, bool eps);
   void axpy_raw(double alpha, const Layout& XL, const double* X,
                 const std::string& ix, double beta, const Layout& YL,
-                double* Y, const std::string& iy);
+                double* Y, const std::string& iy,
+                const double* d_scale = nullptr);
   Layout make_layout(const std::vector<int>& spaces, int split, int gtot);
 
   Dims dims_;

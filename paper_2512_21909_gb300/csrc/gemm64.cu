@@ -23,7 +23,6 @@ namespace cdcc {
 namespace {
 
 constexpr int BK = 16, NT = 256;
-constexpr int SMS = 152;
 
 struct GemmLaunch {
   GemmProb p[GEMM_MAXPROB];
@@ -221,7 +220,7 @@ Plan make_plan(const GemmProb* p, int np, int shape = -1) {
     pl.tn[i] = (p[i].N + pl.bn - 1) / pl.bn;
     ref_tiles += (int64_t)((p[i].M + 63) / 64) * ((p[i].N + 63) / 64);
   }
-  const int64_t want = 4 * SMS;
+  const int64_t want = 4 * (int64_t)sm_count();
   for (int i = 0; i < np; ++i) {
     pl.ks[i] = 1;
     if (p[i].M <= 0 || p[i].N <= 0) continue;
@@ -252,7 +251,8 @@ bool is_thin(const GemmProb& g) {
 int64_t thin_chunk(const GemmProb& g) {
   // about four CTAs per SM over all thin products of a launch, at least
   // four k per thread
-  const int64_t kc = std::max<int64_t>(1024, (g.K + 4 * SMS - 1) / (4 * SMS));
+  const int64_t sms4 = 4 * (int64_t)sm_count();
+  const int64_t kc = std::max<int64_t>(1024, (g.K + sms4 - 1) / sms4);
   return (kc + 255) / 256 * 256;
 }
 

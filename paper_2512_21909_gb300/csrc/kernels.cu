@@ -16,6 +16,26 @@ constexpr int CHUNK = 4096;
 // largest chunk of a permutation / update task per CTA
 int chunk_elems() { return CHUNK; }
 
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    return 152;
+  }
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess ||
+        n <= 0) {
+      (void)cudaGetLastError();
+      n = 152;
+    }
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 // ----------------------------------------------------------- permute / axpy
 namespace {
 
@@ -51,10 +71,12 @@ __device__ __forceinline__ void box_offsets(const PermTask& t, int64_t e,
 __global__ void perm_axpy_kernel(const PermTask* __restrict__ tasks,
                                  const Chunk* __restrict__ chunks,
                                  double alpha, const double* __restrict__ X,
-                                 double beta, double* __restrict__ Y) {
+                                 double beta, double* __restrict__ Y,
+                                 const double* __restrict__ dscale) {
   const Chunk c = chunks[blockIdx.x];
   const PermTask t = tasks[c.task];
   const int64_t end = min(t.n, c.start + (int64_t)c.len);
+  if (dscale) alpha *= *dscale;
   int l[MAXRANK];
   for (int64_t e = c.start + threadIdx.x; e < end; e += blockDim.x) {
     int64_t y, x;
@@ -215,17 +237,17 @@ __global__ void __launch_bounds__(BD_THREADS)
 
 int bd_blocks(int64_t nnz) {
   int64_t b = (nnz + 4095) / 4096;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 8));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, sm_count() * 8));
 }
 
 }  // namespace
 
 int perm_axpy(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
               double alpha, const double* X, double beta, double* Y,
-              cudaStream_t st) {
+              cudaStream_t st, const double* d_scale) {
   if (nchunks <= 0) return 0;
   perm_axpy_kernel<<<nchunks, 256, 0, st>>>(d_tasks, d_chunks, alpha, X, beta,
-                                            Y);
+                                            Y, d_scale);
   return 1;
 }
 
@@ -262,7 +284,7 @@ int lincomb(double* out, const double* const* xs, const double* c, int m,
     pk.p[k] = xs[k];
     pk.c[k] = c[k];
   }
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, sm_count() * 16);
   lincomb_kernel<<<std::max(blocks, 1), 256, 0, st>>>(out, pk, m, n);
   return 1;
 }
@@ -270,7 +292,7 @@ int lincomb(double* out, const double* const* xs, const double* c, int m,
 int axpby(double a, const double* x, double b, double* y, int64_t n,
           cudaStream_t st) {
   if (n <= 0) return 0;
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, sm_count() * 16);
   axpby_kernel<<<blocks, 256, 0, st>>>(a, x, b, y, n);
   return 1;
 }

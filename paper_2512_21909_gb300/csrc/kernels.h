@@ -76,10 +76,11 @@ int oz_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
                     int nslice, void* workspace, unsigned int* d_err,
                     cudaStream_t st);
 
-// Y = beta*Y + alpha*X over the boxes described by tasks/chunks.
+// Y = beta*Y + alpha*s*X over the boxes described by tasks/chunks, with s
+// the device scalar *d_scale (1 when d_scale is null).
 int perm_axpy(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
               double alpha, const double* X, double beta, double* Y,
-              cudaStream_t st);
+              cudaStream_t st, const double* d_scale = nullptr);
 
 // Jacobi step over DPD boxes: s = R / D (D from orbital energies),
 // t += s, err = s, and atomically max |s| into *d_maxbits.
@@ -107,6 +108,10 @@ int batched_dot(const double* G, const double* dL, int nx, int64_t nnz,
                 double* partial, double* d_g, cudaStream_t st);
 
 int chunk_elems();
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// looked up once per device); grids are sized in multiples of it.
+int sm_count();
 
 // Row-batch permutation of the on-the-fly ladder (ladder.cu):
 // X_gc[a][c][b][d] (blocks back to back at xoff[gc]) <-> W[(a,b)][coff[gc] +

@@ -220,6 +220,77 @@ void Engine::ladder(double alpha, Tensor* T, Tensor* L, Tensor* R) {
   if (recording_)
     tape_.push_back({2, alpha, 1.0, T, L, R, "ijcd", "Pac", "ijab"});
   if (record_only_) return;
+  ladder_lin_apply(0, alpha, T, L, false, R);
+}
+
+void Engine::ladder_stored(double alpha, Tensor* T, Tensor* W, Tensor* R) {
+  if (!is_doubles(T->lay) || !is_doubles(R->lay))
+    throw EngineError("ladder_stored: amplitude layouts must be "
+                      "{SO,SO,SV,SV}/2");
+  if (recording_)
+    tape_.push_back({3, alpha, 1.0, T, W, R, "ijcd", "abcd", "ijab"});
+  if (record_only_) return;
+  ladder_lin_apply(0, alpha, T, W, true, R);
+}
+
+void Engine::ladder_lin(int which, int mode, int prec) {
+  LadderLin& st = lin_[which];
+  st.mode = mode;
+  st.prec = prec;
+  st.anchored = false;
+}
+
+// Y += alpha * Lad(X), linearised around the anchor of lin_[which] (see
+// engine.h); with the mode off (or while a tape is recorded) the plain map.
+void Engine::ladder_lin_apply(int which, double alpha, Tensor* X, Tensor* LW,
+                              bool stored, Tensor* Y) {
+  LadderLin& st = lin_[which];
+  if (st.mode == 0 || recording_) {
+    ladder_map(alpha, X, LW, stored, Y);
+    return;
+  }
+  const std::string tag = which == 0 ? "ladlin_f_" : "ladlin_a_";
+  std::vector<int> sp(X->lay.sp, X->lay.sp + X->lay.rank);
+  st.in = tensor(tag + "in", sp, X->lay.split, X->lay.gtot);
+  st.out = tensor(tag + "out", sp, X->lay.split, X->lay.gtot);
+  if (st.mode == 1) {
+    // new anchor: X0 = X, out = Lad_acc(X0)
+    axpy_raw(1.0, X->lay, X->d, "ijab", 0.0, st.in->lay, st.in->d, "ijab");
+    zero(st.out);
+    ladder_map(1.0, X, LW, stored, st.out);
+    st.mode = 2;
+    st.anchored = true;
+  } else {
+    // Y += alpha * Lad_delta(X - X0)
+    st.d = tensor(tag + "d", sp, X->lay.split, X->lay.gtot);
+    axpy_raw(1.0, X->lay, X->d, "ijab", 0.0, st.d->lay, st.d->d, "ijab");
+    axpy_raw(-1.0, st.in->lay, st.in->d, "ijab", 1.0, st.d->lay, st.d->d,
+             "ijab");
+    ++st.d->ver;
+    const int keep = tc_override_;
+    tc_override_ = st.prec;
+    try {
+      ladder_map(alpha, st.d, LW, stored, Y);
+    } catch (...) {
+      tc_override_ = keep;
+      throw;
+    }
+    tc_override_ = keep;
+    st.anchored = false;
+  }
+  axpy_raw(alpha, st.out->lay, st.out->d, "ijab", 1.0, Y->lay, Y->d, "ijab");
+  ++Y->ver;
+}
+
+void Engine::ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
+                        Tensor* Y) {
+  if (stored) {
+    contract(alpha, X, "ijcd", LW, "abcd", 1.0, Y, "ijab");
+    return;
+  }
+  Tensor* T = X;
+  Tensor* L = LW;
+  Tensor* R = Y;
   ++R->ver;
   cudaEvent_t tr_a = nullptr;
   if (prof_on_) {
@@ -241,8 +312,11 @@ void Engine::ladder(double alpha, Tensor* T, Tensor* L, Tensor* R) {
   if (tr_a) {
     cudaEvent_t tr_b = get_event();
     cudaEventRecord(tr_b, st_);
-    trace_pending_.push_back({"ladder on the fly (ijcd,Pac,Pbd->ijab)", tr_a,
-                              tr_b, fl});
+    const int pr = active_precision();
+    trace_pending_.push_back(
+        {std::string("ladder on the fly (ijcd,Pac,Pbd->ijab) [") +
+             (pr >= 12 ? "exact" : pr > 0 ? "split" : "fp64") + "]",
+         tr_a, tr_b, fl});
   }
   release_scratch();
 }

@@ -417,8 +417,9 @@ TcPlan tc_plan(const TcProb* p, int np, int s) {
   }
   for (int i = 0; i < np; ++i) {
     pl.ks[i] = 1;
-    if (tiles < 2 * 152 && pl.nkb[i] >= 8) {
-      int ks = (int)((2 * 152 + tiles - 1) / std::max<int64_t>(tiles, 1));
+    const int64_t sms2 = 2 * (int64_t)sm_count();
+    if (tiles < sms2 && pl.nkb[i] >= 8) {
+      int ks = (int)((sms2 + tiles - 1) / std::max<int64_t>(tiles, 1));
       ks = std::min(ks, pl.nkb[i] / 4);
       pl.ks[i] = std::max(1, std::min(ks, 32));
     }

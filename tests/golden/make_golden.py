@@ -6,6 +6,7 @@ the gradient g_x for every displacement and a seeded sample of Gamma^P,
 t2 and lambda2 elements (packed / dense indices with values).
 
     python tests/golden/make_golden.py 1        # writes tests/golden/c1.json
+    python tests/golden/make_golden.py serving  # writes tests/golden/serving.json
 """
 from __future__ import annotations
 
@@ -53,8 +54,39 @@ def golden(idx: int, nsample: int = 64):
     )
 
 
+def golden_serving(omax: int = 16, nx: int = 2):
+    """FP64 oracle energy and gradient of every serving request with
+    o <= omax (the first 64 requests of the serving workload)."""
+    from synth.serving import serving_jobs, job_system
+    out = {}
+    for sp in serving_jobs():
+        if sp.o > omax:
+            continue
+        s = job_system(sp)
+        L = torch.as_tensor(unpack_dense(s, s.L))
+        h = model.core_from_eps(torch.as_tensor(s.eps), L, s.nocc)
+        t0 = time.time()
+        r = lagrangian.run_all(h, L, s.nocc, tol=1e-11, e_tol=1e-13)
+        dL = make_displacements(s, nx)
+        g = dL @ pack_dense(s, r["G"].numpy())
+        out[str(sp.index)] = dict(o=sp.o, group=sp.group, scale=s.scale,
+                                  e_corr=r["cc"]["E_corr"],
+                                  gradient=g.tolist(),
+                                  oracle_seconds=time.time() - t0)
+        print(sp.index, sp.o, sp.group, r["cc"]["E_corr"], flush=True)
+    return dict(workload="serving requests with o <= %d" % omax, tol=1e-11,
+                nx=nx, requests=out)
+
+
 if __name__ == "__main__":
     for a in sys.argv[1:]:
+        if a == "serving":
+            out = golden_serving()
+            path = os.path.join(HERE, "serving.json")
+            with open(path, "w") as f:
+                json.dump(out, f, indent=1)
+            print("wrote", path)
+            continue
         idx = int(a)
         out = golden(idx)
         path = os.path.join(HERE, f"c{idx}.json")
