@@ -402,3 +402,78 @@ def test_stored_scale_gives_target_mp2_energy():
     L = unpack_dense(s, s.L)
     e = mp2.mp2_energy(s.eps, L, s.nocc)
     assert abs(e - (-0.04 * s.nocc)) < 1e-10
+
+
+# ------------------------------------- DF / Cholesky three-term gradient
+def _df_case(s, nx=2):
+    from synth.df import make_df_inputs
+    M, Kp, dB, dM = make_df_inputs(s, nx)
+    L, h = _sys_dense(s)
+    # three-index integrals of this workload: B = K L per irrep block, with
+    # K the Cholesky factor of the metric (Eq. cv_2ndstep read backwards)
+    B = np.zeros_like(L)
+    P0, off = 0, 0
+    for n in s.chol:
+        K = np.linalg.cholesky(M[off:off + n * n].reshape(n, n))
+        B[P0:P0 + n] = (K @ L[P0:P0 + n].reshape(n, -1)).reshape(n, *L.shape[1:])
+        P0 += n
+        off += n * n
+    dBd = np.stack([unpack_dense(s, x) for x in dB])
+    return L, h, M, dM, B, dBd
+
+
+def _vectors_of(s, M, B):
+    """L = K^{-1} B per irrep block (numpy, for the finite differences)."""
+    L = np.zeros_like(B)
+    P0, off = 0, 0
+    for n in s.chol:
+        K = np.linalg.cholesky(M[off:off + n * n].reshape(n, n))
+        L[P0:P0 + n] = scipy.linalg.solve_triangular(
+            K, B[P0:P0 + n].reshape(n, -1), lower=True).reshape(
+                n, *B.shape[1:])
+        P0 += n
+        off += n * n
+    return L
+
+
+@pytest.mark.parametrize("occ,vir,chol,seed", [((3,), (7,), (12,), 61),
+                                               ((2, 1, 1, 1), (4, 3, 3, 2),
+                                                (8, 6, 6, 5), 62)])
+def test_df_gradient_equals_differentiated_vector_form(occ, vir, chol, seed):
+    from oracle import df
+    s = random_system(list(occ), list(vir), list(chol), seed=seed, scale=0.4)
+    L, h, M, dM, B, dB = _df_case(s)
+    assert np.abs(_vectors_of(s, M, B) - L).max() < 1e-13
+    r = lagrangian.run_all(h, T(L), s.nocc, tol=1e-12, e_tol=1e-13)
+    g = df.df_gradient(r["G"], T(L), M, s.chol, T(dB), T(dM)).numpy()
+    for x in range(2):
+        # dL/dx of L(x) = chol(M + x dM)^{-1} (B + x dB), Richardson
+        fd = []
+        for step in (1e-3, 5e-4):
+            Lp = _vectors_of(s, M + step * dM[x], B + step * dB[x])
+            Lm = _vectors_of(s, M - step * dM[x], B - step * dB[x])
+            fd.append((Lp - Lm) / (2 * step))
+        dL = (4.0 * fd[1] - fd[0]) / 3.0
+        ref = float(np.sum(r["G"].numpy() * dL))
+        assert abs(g[x] - ref) < 1e-9, (x, g[x], ref)
+    # a planted mistake in the metric term is caught
+    g_bad = df.df_gradient(r["G"], T(L), M, s.chol, T(dB), T(2.0 * dM))
+    assert np.abs(g_bad.numpy() - g).max() > 1e-4
+
+
+def test_df_gradient_matches_energy_finite_difference():
+    from oracle import df
+    s = random_system([2, 1, 1, 1], [4, 3, 3, 2], [8, 6, 6, 5], seed=63,
+                      scale=0.4)
+    L, h, M, dM, B, dB = _df_case(s)
+    o = s.nocc
+    r = lagrangian.run_all(h, T(L), o, tol=1e-12, e_tol=1e-13)
+    g = df.df_gradient(r["G"], T(L), M, s.chol, T(dB), T(dM)).numpy()
+
+    def energy(x, k):
+        Lx = _vectors_of(s, M + x * dM[k], B + x * dB[k])
+        return ccsd.solve_ccsd(h, T(Lx), o, tol=1e-13, e_tol=1e-14)["E"]
+    for k in range(2):
+        fd = [(energy(st, k) - energy(-st, k)) / (2 * st)
+              for st in (1e-3, 5e-4)]
+        assert abs(g[k] - (4.0 * fd[1] - fd[0]) / 3.0) < 1e-8
