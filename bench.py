@@ -464,12 +464,37 @@ def run_ours(args, rank, ws):
             "max_abs_dg_vs_this_run": float(np.abs(o_g - g).max()),
             "ladder_tflops": olad[1] / olad[0] / 1e12 if olad[0] else None})
 
+    # ---- error report of the --precision schedule (untimed)
+    err_est = None
+    if args.error_estimate:
+        o = cdcc.cdcc_default_options()
+        o.precision = prec_code(cdcc, args.precision)
+        o.ladder_linearize = 1 if lin else 0
+        ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
+                                s.orb_irrep, s.eps, s.chol_irrep, run.L_d,
+                                options=o)
+        cdcc.gradient(ctx, run.dL_d)
+        t0 = time.perf_counter()
+        dE, dg = cdcc.cdcc_error_estimate(ctx, run.dL_d)
+        err_est = {"dE": dE, "max_dg": float(np.abs(dg).max()),
+                   "seconds": time.perf_counter() - t0,
+                   "what": "|E64(t)-E(t)| + |<lambda,R64(t)>| and "
+                           "|<Gamma64-Gamma, dL>| against FP64 at the "
+                           "converged t, lambda"}
+        cdcc.cd_ccsd_free(ctx)
+
     # ---- mixed (this schedule) vs plain FP64 GPU path on the comparison
-    # workload, one gradient each after one warm-up of each
+    # workload, one gradient each after one warm-up of each; the timed
+    # workload's inputs leave the device first, so that each schedule picks
+    # its ladder mode from the free memory of a dedicated device
     compare = None
+    peak_gb = torch.cuda.max_memory_allocated(dev) / 1e9
     if args.compare not in ("none", "") and args.precision != "fp64" \
             and not args.symmetry_ignored:
         cfg2 = int(args.compare)
+        if cfg2 != args.config:
+            run.L_d = run.dL_d = None
+            torch.cuda.empty_cache()
         r2 = run if cfg2 == args.config else Runner(cfg2, dev)
         res = {}
         for p in (args.precision, "fp64"):
@@ -495,25 +520,6 @@ def run_ours(args, rank, ws):
                     "6.4e12 flop per application) it would take about half "
                     "an hour per gradient"}
         del r2
-
-    # ---- error report of the --precision schedule (untimed)
-    err_est = None
-    if args.error_estimate:
-        o = cdcc.cdcc_default_options()
-        o.precision = prec_code(cdcc, args.precision)
-        o.ladder_linearize = 1 if lin else 0
-        ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
-                                s.orb_irrep, s.eps, s.chol_irrep, run.L_d,
-                                options=o)
-        cdcc.gradient(ctx, run.dL_d)
-        t0 = time.perf_counter()
-        dE, dg = cdcc.cdcc_error_estimate(ctx, run.dL_d)
-        err_est = {"dE": dE, "max_dg": float(np.abs(dg).max()),
-                   "seconds": time.perf_counter() - t0,
-                   "what": "|E64(t)-E(t)| + |<lambda,R64(t)>| and "
-                           "|<Gamma64-Gamma, dL>| against FP64 at the "
-                           "converged t, lambda"}
-        cdcc.cd_ccsd_free(ctx)
 
     if rank != 0:
         return
@@ -553,7 +559,7 @@ def run_ours(args, rank, ws):
         "iterations": dict(zip(["ccsd_bf16x3", "ccsd_accurate",
                                 "lambda_bf16x3", "lambda_accurate"],
                                info0["solver"])),
-        "peak_device_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
+        "peak_device_gb": peak_gb,
         "ladder": {"seconds_per_step": lad[0], "flops_per_step": lad[1],
                    "tflops": lad[1] / lad[0] / 1e12 if lad[0] > 0 else None,
                    "share_of_step": lad[0] / t50,

@@ -190,6 +190,31 @@ cdcc_status contract_dL(cdcc_ctx *ctx, int nx, const int32_t *x_irrep,
                         const double *dL, double *g);
 
 /*
+ * Gradient in the density-fitting / Cholesky three-term form (Sec. 2.1 Eqs.
+ * dfcd, cv_2ndstep and eri_cddf_der; Sec. 2.6 Eq. 2el_grad_cont), the
+ * paper's own route: the Cholesky vectors are L^P = sum_R K^{-1}_PR B^R with
+ * three-index integrals B^R_pq = (R|pq) and the metric M_PQ = (P|Q) =
+ * (K K^T)_PQ (K lower triangular, M block diagonal by the irrep of P).  A
+ * displacement changes B and M; with Jt = K^{-T} Gamma, Ltilde = K^{-T} L
+ * and W_PQ = 1/2 sum_pq Ltilde^P_pq Jt^Q_pq,
+ *     g[x] = sum_P <Jt^P, dB_x^P> - sum_PQ W_PQ dM_x,PQ .
+ * It equals contract_dL with dL_x = d/dx [chol(M + x dM)^{-1} (B + x dB)].
+ *   metric   M: for each irrep G, the nchol(G) x nchol(G) block, row-major,
+ *            blocks back to back (cdcc_metric_size doubles); symmetric
+ *            positive definite, else CDCC_EINVAL.  L given to cd_ccsd_init
+ *            must be K^{-1} B for this M (K its Cholesky factor).
+ *   nx       number of displacements (totally symmetric)
+ *   dB       nx packed three-index derivatives (L-pattern, G_x = 0)
+ *   dM       nx metric derivatives (packed as metric, symmetric blocks)
+ *   g        [nx] output
+ * The factorisation runs on the device in FP64, the transformations in the
+ * accurate arithmetic of the schedule.  Requires build_density.
+ */
+size_t cdcc_metric_size(const cdcc_ctx *ctx);
+cdcc_status contract_df(cdcc_ctx *ctx, const double *metric, int nx,
+                        const double *dB, const double *dM, double *g);
+
+/*
  * Error report of a result (the precision schedule of Sec. 2 / cdcc_options):
  * what the schedule's reduced-precision arithmetic changed, measured against
  * FP64 DFMA arithmetic at the same converged amplitudes t and multipliers

@@ -269,6 +269,30 @@ def contract_dL(ctx, dL, nx=None, x_irrep=None):
     return g
 
 
+def cdcc_metric_size(ctx) -> int:
+    lib = load()
+    lib.cdcc_metric_size.argtypes = [ctypes.c_void_p]
+    lib.cdcc_metric_size.restype = ctypes.c_size_t
+    return int(lib.cdcc_metric_size(ctx.handle))
+
+
+def contract_df(ctx, metric, dB, dM):
+    """Three-term DF/CD gradient (see include/cdcc.h): metric packed,
+    dB (nx, packed), dM (nx, metric size); host or device arrays."""
+    lib = load()
+    lib.contract_df.argtypes = [ctypes.c_void_p] * 2 + [ctypes.c_int] + \
+        [ctypes.c_void_p] * 3
+    lib.contract_df.restype = ctypes.c_int
+    Mp, Mk = _ptr(_f64(metric))
+    dBp, dBk = _ptr(_f64(dB))
+    dMp, dMk = _ptr(_f64(dM))
+    nx = int(dB.shape[0])
+    g = np.zeros(max(nx, 1))
+    _check(ctx, lib.contract_df(ctx.handle, Mp, nx, dBp, dMp,
+                                g.ctypes.data_as(ctypes.c_void_p)))
+    return g[:nx]
+
+
 def cdcc_error_estimate(ctx, dL=None, nx=None, x_irrep=None):
     """(dE, dg[nx]): change of E and g caused by the schedule's reduced
     precision, measured against FP64 at the converged t and lambda."""

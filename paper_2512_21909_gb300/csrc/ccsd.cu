@@ -840,6 +840,95 @@ void run_contract(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   std::memcpy(g, out.data(), nx * 8);
 }
 
+// sum_e A[e] X_x[e] for nx vectors X_x of n doubles back to back (host or
+// device memory), 8 at a time through the batched dot kernel.
+void dots_with(cdcc_ctx* c, const double* A, const double* X, int nx,
+               int64_t n, double* out) {
+  Engine& e = *c->eng;
+  if (nx <= 0) return;
+  if (n == 0) {
+    for (int x = 0; x < nx; ++x) out[x] = 0.0;
+    return;
+  }
+  const bool dev = is_device_ptr(X);
+  const int XB = 8;
+  double* stage = dev ? nullptr : e.scratch((int64_t)XB * n);
+  double* d_g = e.scratch(XB);
+  double* part = e.scratch(batched_dot_partial_doubles(n, XB));
+  std::vector<double> tmp(XB);
+  for (int x = 0; x < nx; x += XB) {
+    const int cnt = std::min(XB, nx - x);
+    const double* src = X + (int64_t)x * n;
+    if (!dev) {
+      CK(cudaMemcpyAsync(stage, src, (size_t)cnt * n * 8,
+                         cudaMemcpyHostToDevice, c->st));
+      src = stage;
+    }
+    e.timed(Engine::K_DOT, 8.0 * (cnt + 1) * n, [&] {
+      return batched_dot(A, src, cnt, n, part, d_g, c->st);
+    });
+    CK(cudaMemcpyAsync(tmp.data(), d_g, cnt * 8, cudaMemcpyDeviceToHost,
+                       c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int k = 0; k < cnt; ++k) out[x + k] = tmp[k];
+  }
+  e.release_scratch();
+}
+
+// Three-term gradient of the density-fitting / Cholesky form (Sec. 2.1
+// Eqs. dfcd, cv_2ndstep, eri_cddf_der; Sec. 2.6 Eq. 2el_grad_cont): with
+// L = K^{-1} B and M = K K^T,
+//   g_x = sum_P <Jt^P, dB_x^P> - sum_PQ W_PQ dM_x,PQ,
+//   Jt = K^{-T} Gamma,  Ltilde = K^{-T} L,  W = 1/2 Ltilde Jt^T,
+// in the accurate arithmetic of the schedule.
+void run_contract_df(cdcc_ctx* c, const double* metric, int nx,
+                     const double* dB, const double* dM, double* g) {
+  Engine& e = *c->eng;
+  PhaseTimer pt(c, 3);
+  Tensor* Mt = e.tensor("df_M", {SQ, SQ}, 1);
+  Tensor* Kt = e.tensor("df_KinvT", {SQ, SQ}, 1);
+  MetricBlocks mb;
+  std::memset(&mb, 0, sizeof(mb));
+  int64_t off = 0;
+  for (int G = 0; G < c->hd.h; ++G) {
+    if (Mt->lay.blk_off[G] != off)
+      throw StatusError(CDCC_EINVAL, "internal: metric layout");
+    mb.off[G] = off;
+    mb.n[G] = c->dims.n[SQ][G];
+    off += (int64_t)mb.n[G] * mb.n[G];
+  }
+  mb.nblk = c->hd.h;
+  if (off != Mt->lay.size)
+    throw StatusError(CDCC_EINVAL, "internal: metric size");
+  copy_in(c, Mt->d, metric, off);
+  CK(cudaMemsetAsync(c->d_err + 1, 0, 4, c->st));
+  e.timed(Engine::K_OTHER, 16.0 * off, [&] {
+    return metric_factor(Mt->d, Kt->d, mb, c->d_err + 1, c->st);
+  });
+  unsigned int bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->d_err + 1, 4, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (bad)
+    throw StatusError(CDCC_EINVAL, "metric is not positive definite");
+  ++Mt->ver;
+  ++Kt->ver;
+  const int prec = e.precision();
+  e.set_precision(exact_prec(c));
+  Tensor* Jt = e.tensor("df_Jt", {SQ, SA, SA}, 1);
+  Tensor* Lt = e.tensor("df_Lt", {SQ, SA, SA}, 1);
+  Tensor* W = e.tensor("df_W", {SQ, SQ}, 1);
+  e.contract(1.0, Kt, "PQ", c->Gsym, "Qpq", 0.0, Jt, "Ppq");
+  e.contract(1.0, Kt, "PQ", c->Lpk, "Qpq", 0.0, Lt, "Ppq");
+  e.contract(0.5, Lt, "Ppq", Jt, "Qpq", 0.0, W, "PQ");
+  e.set_precision(prec);
+  std::vector<double> gb(std::max(nx, 1)), gm(std::max(nx, 1));
+  dots_with(c, Jt->d, dB, nx, Jt->lay.size, gb.data());
+  dots_with(c, W->d, dM, nx, W->lay.size, gm.data());
+  pt.stop();
+  check_device_error(c);
+  for (int x = 0; x < nx; ++x) g[x] = gb[x] - gm[x];
+}
+
 // What the reduced-precision arithmetic of the schedule changed, measured
 // against FP64 DFMA arithmetic at the same converged (t, lambda):
 //   dE   = |E64(t) - E(t)| + |<lambda, R64(t)>|: the FP64 equations leave a
@@ -1308,6 +1397,25 @@ cdcc_status cdcc_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
   }
   if (nx < 0 || (nx > 0 && (!dL || !dg))) return CDCC_EINVAL;
   return guarded(c, [&] { run_error_estimate(c, nx, x_irrep, dL, dE, dg); });
+}
+
+size_t cdcc_metric_size(const cdcc_ctx* c) {
+  if (!c || c->state < 1) return 0;
+  size_t s = 0;
+  for (int G = 0; G < c->hd.h; ++G)
+    s += (size_t)c->dims.n[SQ][G] * c->dims.n[SQ][G];
+  return s;
+}
+
+cdcc_status contract_df(cdcc_ctx* c, const double* metric, int nx,
+                        const double* dB, const double* dM, double* g) {
+  if (!c || !metric) return CDCC_EINVAL;
+  if (c->state < 4) {
+    c->err = "contract_df before build_density";
+    return CDCC_ESTATE;
+  }
+  if (nx < 0 || (nx > 0 && (!dB || !dM || !g))) return CDCC_EINVAL;
+  return guarded(c, [&] { run_contract_df(c, metric, nx, dB, dM, g); });
 }
 
 cdcc_status cdcc_energy_error(cdcc_ctx* c, double* dE) {

@@ -59,6 +59,7 @@ Engine::~Engine() {
   for (auto& b : pool_) al.release(b.d, (size_t)b.n * 8);
   if (lad_x_) al.release(lad_x_, (size_t)lad_n_ * 8);
   if (lad_w_) al.release(lad_w_, (size_t)lad_n_ * 8);
+  if (lad_ws_) al.release(lad_ws_, lad_ws_bytes_);
   for (auto& kv : slice_cache_) {
     al.release(kv.second.data, kv.second.bytes);
     if (kv.second.exps) al.release(kv.second.exps, kv.second.ebytes);
@@ -629,11 +630,12 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
 }
 
 // Route the blocks of one product (they write disjoint parts of C) to the
-// tensor cores or the FP64 kernel and launch them.  Tensor cores only take
-// matrix-shaped blocks (both output sides >= 32, K >= 32; K is padded to the
-// 64-wide slice rows): thin products (dots, outer products, o x o results,
-// sums over one occupied index) stay on the FP64 path with split K.  Returns
-// the path taken.
+// tensor cores or the FP64 kernel and launch them.  Tensor cores take every
+// matrix-shaped block (both output sides >= 32; a short K is padded to the
+// 64-wide stage, which costs MMAs the tensor pipe has to spare where the
+// FP64 pipe has none): thin products (dots, outer products, o x o results,
+// one output side of at most 16) stay on the FP64 path.  Returns the path
+// taken.
 const char* Engine::run_gemms(const GemmProb* probs, int np, const Mat& mp,
                               const Mat& mq, double alpha, double beta) {
   double fl = 0;
@@ -648,7 +650,7 @@ const char* Engine::run_gemms(const GemmProb* probs, int np, const Mat& mp,
   for (int i = 0; i < np; ++i) {
     const GemmProb& g = probs[i];
     if (prec > 0 && std::min(g.M, g.N) >= 32 &&
-        std::max(g.M, g.N) >= 64 && g.K >= 32) {
+        std::max(g.M, g.N) >= 64 && g.K >= 1) {
       fl_tc += 2.0 * g.M * (double)g.N * g.K;
       ptc[ntc++] = g;
     } else {

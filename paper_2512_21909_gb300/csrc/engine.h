@@ -247,6 +247,15 @@ class Engine {
   };
   std::vector<LadBatch> ladder_batches(const Layout& TL);
   double ladder_build(const LadBatch& b, Tensor* L);   // -> lad_w_
+  // float-slice arithmetic: the build GEMM writes the BF16 slices of the
+  // batch rows directly (lad_ws_) and the apply reads them; false when a
+  // block is too small for the tensor-core route
+  bool ladder_fusable(const LadBatch& b, const Layout& TL, const Layout& LL);
+  double ladder_build_sliced(const LadBatch& b, Tensor* L, int ns);
+  void ladder_apply_sliced(const LadBatch& b, double alpha, Tensor* X,
+                           Tensor* Y, int ns);
+  void* lad_ws_ = nullptr;
+  size_t lad_ws_bytes_ = 0;
   void ladder_perm(const LadBatch& b, bool inverse, const double* src,
                    double* dst);
   void ladder_apply_batch(const LadBatch& b, double alpha, Tensor* X,

@@ -326,18 +326,229 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------- narrow
+// Products with one output side of at most 16 (sums over or into one
+// occupied index, o x v results with long K): memory bound, so the tiles of
+// the square kernel would waste most of their work.  Each CTA takes 128
+// rows of the large side ("big" operand X, K values per row) and all S <= 16
+// columns of the small side (operand Y, K x S), streams K in chunks of 32
+// through shared memory with coalesced loads, and every thread accumulates
+// one row of S outputs.  Long K is split over CTAs (fixed-order reduction).
+constexpr int NR_ROWS = 128, NR_KC = 32, NR_S = 16;
+
+bool is_narrow(const GemmProb& g) {
+  return g.M > 0 && g.N > 0 && std::min(g.M, g.N) <= NR_S;
+}
+
+struct NarrowLaunch {
+  GemmProb p[GEMM_MAXPROB];
+  int first[GEMM_MAXPROB + 1];   // first CTA of each product
+  int rt[GEMM_MAXPROB];          // row tiles of the large side
+  int ks[GEMM_MAXPROB];          // K splits
+  int64_t kc[GEMM_MAXPROB];      // K per split (multiple of NR_KC)
+  int64_t poff[GEMM_MAXPROB];    // split-K partials (logical C order)
+  int np;
+  double alpha, beta;
+  double* part;
+};
+
+// SB >= S bounds the small side (4, 8 or 16) so that the accumulators stay
+// in registers and no multiply-add is spent on padding: GB300 issues 2 DFMA
+// per clock per SM, so these products are bound by their useful FMAs.
+template <int SB>
+__global__ void __launch_bounds__(NR_ROWS)
+    narrow_kernel(const __grid_constant__ NarrowLaunch T) {
+  __shared__ double xs[NR_ROWS][NR_KC + 1];
+  __shared__ double ys[NR_KC][NR_S];
+  int i = 0;
+  while (i + 1 < T.np && (int)blockIdx.x >= T.first[i + 1]) ++i;
+  const GemmProb& P = T.p[i];
+  const int blk = (int)blockIdx.x - T.first[i];
+  const int ksi = blk % T.ks[i];
+  const int r0 = (blk / T.ks[i]) * NR_ROWS;
+  const bool bigA = P.N <= P.M;            // large side = M (operand A)
+  const int R = bigA ? P.M : P.N;          // rows of the large side
+  const int S = bigA ? P.N : P.M;
+  // X(r,k): large operand; Y(k,s): small operand
+  const double* X = bigA ? P.A : P.B;
+  const double* Y = bigA ? P.B : P.A;
+  const int64_t ldx = bigA ? P.lda : P.ldb;
+  const int64_t ldy = bigA ? P.ldb : P.lda;
+  // X(r,k) = xk ? X[r*ldx + k] : X[k*ldx + r]
+  const bool xk = bigA ? (P.ta == 0) : (P.tb != 0);
+  // Y(k,s) = ys_k ? Y[s*ldy + k] : Y[k*ldy + s]
+  const bool yk = bigA ? (P.tb != 0) : (P.ta == 0);
+  const int64_t k0 = (int64_t)ksi * T.kc[i];
+  const int64_t k1 = min((int64_t)P.K, k0 + T.kc[i]);
+  const int t = threadIdx.x;
+  double acc[SB];
+#pragma unroll
+  for (int q = 0; q < SB; ++q) acc[q] = 0.0;
+  for (int64_t kb = k0; kb < k1; kb += NR_KC) {
+    const int nk = (int)min((int64_t)NR_KC, k1 - kb);
+    __syncthreads();
+    // large operand tile: 128 rows x 32 k, coalesced along the stored order
+    for (int e = t; e < NR_ROWS * NR_KC; e += NR_ROWS) {
+      int rr, kk;
+      if (xk) {
+        rr = e / NR_KC;
+        kk = e - rr * NR_KC;
+      } else {
+        kk = e / NR_ROWS;
+        rr = e - kk * NR_ROWS;
+      }
+      const int r = r0 + rr;
+      double v = 0.0;
+      if (r < R && kk < nk)
+        v = xk ? X[(int64_t)r * ldx + kb + kk] : X[(kb + kk) * ldx + r];
+      xs[rr][kk] = v;
+    }
+    for (int e = t; e < NR_KC * NR_S; e += NR_ROWS) {
+      int kk, q;
+      if (yk) {
+        q = e / NR_KC;
+        kk = e - q * NR_KC;
+      } else {
+        kk = e / NR_S;
+        q = e - kk * NR_S;
+      }
+      double v = 0.0;
+      if (q < S && kk < nk)
+        v = yk ? Y[(int64_t)q * ldy + kb + kk] : Y[(kb + kk) * ldy + q];
+      ys[kk][q] = v;
+    }
+    __syncthreads();
+    if (r0 + t < R) {
+      for (int kk = 0; kk < nk; ++kk) {
+        const double x = xs[t][kk];
+#pragma unroll
+        for (int q = 0; q < SB; ++q)
+          if (q < S) acc[q] = fma(x, ys[kk][q], acc[q]);
+      }
+    }
+  }
+  const int r = r0 + t;
+  if (r >= R) return;
+#pragma unroll
+  for (int q = 0; q < SB; ++q) {
+    if (q >= S) break;
+    const int m = bigA ? r : q, n = bigA ? q : r;
+    if (T.ks[i] > 1) {
+      T.part[T.poff[i] + (int64_t)ksi * P.M * P.N + (int64_t)m * P.N + n] =
+          acc[q];
+    } else {
+      double* c = P.C + (int64_t)m * P.ldc + n;
+      const double v = T.alpha * acc[q];
+      *c = (T.beta == 0.0) ? v : fma(T.beta, *c, v);
+    }
+  }
+}
+
+void narrow_plan(const GemmProb& g, int np_total, int& rt, int& ks,
+                 int64_t& kc) {
+  const int R = std::max(g.M, g.N);   // the large side (the small one <= 16)
+  rt = (R + NR_ROWS - 1) / NR_ROWS;
+  if (g.K <= 0) {   // empty sum (an irrep without Cholesky vectors): C = beta C
+    ks = 1;
+    kc = NR_KC;
+    return;
+  }
+  const int64_t want = 4 * (int64_t)sm_count();
+  ks = 1;
+  const int64_t have = (int64_t)rt * std::max(1, np_total);
+  if (have < want && g.K >= 4 * 256) {
+    const int64_t kmax = (g.K + 255) / 256;
+    ks = (int)std::min<int64_t>(kmax, (want + have - 1) / have);
+    ks = std::max(1, std::min(ks, 256));
+  }
+  kc = ((g.K + ks - 1) / ks + NR_KC - 1) / NR_KC * NR_KC;
+  ks = (int)((g.K + kc - 1) / kc);
+}
+
 int split_thin(const GemmProb* p, int np, GemmProb* reg, GemmProb* thin,
-               int* nthin) {
+               int* nthin, GemmProb* narrow = nullptr, int* nnarrow = nullptr) {
   int nr = 0;
   *nthin = 0;
+  if (nnarrow) *nnarrow = 0;
   for (int i = 0; i < np; ++i) {
     if (p[i].M <= 0 || p[i].N <= 0) continue;
     if (is_thin(p[i]))
       thin[(*nthin)++] = p[i];
+    else if (narrow && is_narrow(p[i]))
+      narrow[(*nnarrow)++] = p[i];
     else
       reg[nr++] = p[i];
   }
   return nr;
+}
+
+int64_t narrow_scratch(const GemmProb* q, int nn) {
+  int64_t s = 0;
+  for (int i = 0; i < nn; ++i) {
+    int rt, ks;
+    int64_t kc;
+    narrow_plan(q[i], nn, rt, ks, kc);
+    if (ks > 1) s += (int64_t)ks * q[i].M * q[i].N;
+  }
+  return s;
+}
+
+int launch_narrow(const GemmProb* q, int nn, double alpha, double beta,
+                  double* part, cudaStream_t st) {
+  if (nn <= 0) return 0;
+  NarrowLaunch T;
+  std::memset(&T, 0, sizeof(T));
+  ReduceLaunch R;
+  std::memset(&R, 0, sizeof(R));
+  T.alpha = R.alpha = alpha;
+  T.beta = R.beta = beta;
+  T.part = part;
+  R.scratch = part;
+  int nblk = 0, nr = 0;
+  int64_t off = 0, relem = 0;
+  for (int i = 0; i < nn; ++i) {
+    int rt, ks;
+    int64_t kc;
+    narrow_plan(q[i], nn, rt, ks, kc);
+    T.p[i] = q[i];
+    T.first[i] = nblk;
+    T.rt[i] = rt;
+    T.ks[i] = ks;
+    T.kc[i] = kc;
+    T.poff[i] = ks > 1 ? off : 0;
+    nblk += rt * ks;
+    if (ks > 1) {
+      R.C[nr] = q[i].C;
+      R.M[nr] = q[i].M;
+      R.N[nr] = q[i].N;
+      R.ldc[nr] = q[i].ldc;
+      R.ks[nr] = ks;
+      R.poff[nr] = off;
+      R.elem0[nr] = relem;
+      relem += (int64_t)q[i].M * q[i].N;
+      off += (int64_t)ks * q[i].M * q[i].N;
+      ++nr;
+    }
+  }
+  T.first[nn] = nblk;
+  T.np = nn;
+  int smax = 0;
+  for (int i = 0; i < nn; ++i) smax = std::max(smax, std::min(q[i].M, q[i].N));
+  if (smax <= 4)
+    narrow_kernel<4><<<nblk, NR_ROWS, 0, st>>>(T);
+  else if (smax <= 8)
+    narrow_kernel<8><<<nblk, NR_ROWS, 0, st>>>(T);
+  else
+    narrow_kernel<16><<<nblk, NR_ROWS, 0, st>>>(T);
+  int launches = 1;
+  if (nr > 0) {
+    R.np = nr;
+    R.elem0[nr] = relem;
+    const int blocks = (int)std::min<int64_t>((relem + 255) / 256, 1024);
+    splitk_reduce_kernel<<<std::max(blocks, 1), 256, 0, st>>>(R);
+    ++launches;
+  }
+  return launches;
 }
 
 int grouped_tiles(const GemmProb* p, int np, double alpha, double beta,
@@ -346,10 +557,10 @@ int grouped_tiles(const GemmProb* p, int np, double alpha, double beta,
 }  // namespace
 
 int64_t gemm_scratch_doubles(const GemmProb* p, int np) {
-  GemmProb reg[GEMM_MAXPROB], thin[GEMM_MAXPROB];
-  int nt;
-  const int nr = split_thin(p, np, reg, thin, &nt);
-  int64_t s = make_plan(reg, nr).scratch;
+  GemmProb reg[GEMM_MAXPROB], thin[GEMM_MAXPROB], nar[GEMM_MAXPROB];
+  int nt, nn;
+  const int nr = split_thin(p, np, reg, thin, &nt, nar, &nn);
+  int64_t s = make_plan(reg, nr).scratch + narrow_scratch(nar, nn);
   for (int i = 0; i < nt; ++i)
     s += (int64_t)thin_blocks(thin[i]) * thin[i].M * thin[i].N;
   return s;
@@ -357,12 +568,14 @@ int64_t gemm_scratch_doubles(const GemmProb* p, int np) {
 
 int gemm64_grouped(const GemmProb* p, int np, double alpha, double beta,
                    double* scratch, cudaStream_t st) {
-  GemmProb reg[GEMM_MAXPROB], thin[GEMM_MAXPROB];
-  int nt;
-  const int nr = split_thin(p, np, reg, thin, &nt);
+  GemmProb reg[GEMM_MAXPROB], thin[GEMM_MAXPROB], nar[GEMM_MAXPROB];
+  int nt, nn;
+  const int nr = split_thin(p, np, reg, thin, &nt, nar, &nn);
   int launches = grouped_tiles(reg, nr, alpha, beta, scratch, st);
+  const int64_t reg_scratch = make_plan(reg, nr).scratch;
+  launches += launch_narrow(nar, nn, alpha, beta, scratch + reg_scratch, st);
   if (nt == 0) return launches;
-  double* tpart = scratch + make_plan(reg, nr).scratch;
+  double* tpart = scratch + reg_scratch + narrow_scratch(nar, nn);
   ReduceLaunch R;
   std::memset(&R, 0, sizeof(R));
   R.alpha = alpha;

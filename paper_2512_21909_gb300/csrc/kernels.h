@@ -57,6 +57,19 @@ int64_t tc_sliced_scratch_doubles(const TcProb* p, int np, int nslice);
 int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
                    int nslice, unsigned int* d_err, cudaStream_t st);
 
+// Fused build of on-the-fly ladder rows (tc_gemm.cu): the product of
+// problem i is X_gc[(a,c),(b,d)] (a of the batch, M = na*nc, N = nb*nd) and
+// its element goes, cut into `ns` BF16 slices, to row a*nb + b, column
+// coff + c*nd + d of the K-major slices W[ns][rows][Kp] of the batch's
+// (ab|cd) rows (the B operand of the ladder product).
+struct TcLadEpi {
+  void* W;            // __nv_bfloat16 [ns][rows][Kp]
+  int64_t rows, Kp, coff;
+  int nc, nd, nb, ns;
+};
+int tc_gemm_ladder(const TcProb* p, int np, int nslice, const TcLadEpi* epi,
+                   unsigned int* d_err, cudaStream_t st);
+
 // Split-precision tensor-core GEMM (tc_gemm.cu): same semantics as
 // gemm64_grouped, at most 8 products, nslice BF16 slices per operand (1-3).
 // `workspace` holds tc_workspace_bytes() bytes of BF16 slices, `scratch`
@@ -108,6 +121,18 @@ int batched_dot(const double* G, const double* dL, int nx, int64_t nnz,
                 double* partial, double* d_g, cudaStream_t st);
 
 int chunk_elems();
+
+// Metric blocks of the density-fitting form (df.cu): block b is the
+// n[b] x n[b] row-major matrix at offset off[b].  metric_factor replaces M
+// by its lower Cholesky factor K (upper triangle zeroed; *d_err = 1 if a
+// block is not positive definite) and writes KinvT = (K^{-1})^T.
+struct MetricBlocks {
+  int64_t off[MAXIRR];
+  int n[MAXIRR];
+  int nblk;
+};
+int metric_factor(double* M, double* KinvT, const MetricBlocks& B,
+                  unsigned int* d_err, cudaStream_t st);
 
 // Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
 // looked up once per device); grids are sized in multiples of it.

@@ -186,6 +186,170 @@ double Engine::ladder_build(const LadBatch& b, Tensor* L) {
   return fl;
 }
 
+namespace {
+bool tc_shape(int64_t M, int64_t N, int64_t K) {
+  return std::min(M, N) >= 32 && std::max(M, N) >= 64 && K >= 32;
+}
+}  // namespace
+
+bool Engine::ladder_fusable(const LadBatch& b, const Layout& TL,
+                            const Layout& LL) {
+  const int prec = active_precision();
+  if (prec < 1 || prec > 3 || !d_err) return false;
+  const int G = b.G, ga = b.ga, gb = ga ^ G;
+  if (!tc_shape(TL.nrow[G], b.rows, TL.ncol[G])) return false;
+  const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
+  for (int gc = 0; gc < dims_.h; ++gc) {
+    const int gd = gc ^ G, Gp = ga ^ gc;
+    const int64_t M = (int64_t)na * dims_.n[SV][gc];
+    const int64_t N = (int64_t)nb * dims_.n[SV][gd];
+    const int64_t K = LL.nrow[Gp];
+    if (M * N == 0 || K == 0) continue;
+    if (!tc_shape(M, N, K)) return false;
+  }
+  return true;
+}
+
+// Batch rows of (ab|cd) as ns BF16 slices [ns][rows][Kp] (lad_ws_), written
+// by the epilogue of the build GEMM; returns its flops.
+double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns) {
+  const int h = dims_.h, G = b.G, ga = b.ga, gb = ga ^ G;
+  const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
+  const Layout& LL = L->lay;
+  int64_t ncol = 0;
+  for (int gc = 0; gc < h; ++gc)
+    ncol += (int64_t)dims_.n[SV][gc] * dims_.n[SV][gc ^ G];
+  const int64_t Kp = slice_kp((int)ncol);
+  const size_t need = (size_t)ns * b.rows * Kp * 2;
+  if (need > lad_ws_bytes_) {
+    if (lad_ws_) al.release(lad_ws_, lad_ws_bytes_);
+    lad_ws_ = al.alloc(need);
+    lad_ws_bytes_ = need;
+  }
+  // zero padding columns [ncol, Kp) and, for an irrep without Cholesky
+  // vectors, the whole batch ((ac|bd) = 0 there)
+  bool holes = false;
+  for (int gc = 0; gc < h; ++gc) {
+    const int64_t M = (int64_t)na * dims_.n[SV][gc];
+    const int64_t N = (int64_t)nb * dims_.n[SV][gc ^ G];
+    if (M * N > 0 && LL.nrow[ga ^ gc] == 0) holes = true;
+  }
+  if (holes)
+    LCK(cudaMemsetAsync(lad_ws_, 0, need, st_));
+  else if (Kp > ncol)
+    LCK(cudaMemset2DAsync((uint8_t*)lad_ws_ + ncol * 2, (size_t)Kp * 2, 0,
+                          (size_t)(Kp - ncol) * 2, (size_t)ns * b.rows, st_));
+  TcProb tp[GEMM_MAXPROB];
+  TcLadEpi ep[GEMM_MAXPROB];
+  int np = 0;
+  int64_t coff = 0, wsb = 1024;
+  for (int gc = 0; gc < h; ++gc) {
+    const int gd = gc ^ G, Gp = ga ^ gc;
+    const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gd];
+    const int64_t M = (int64_t)na * nc, N = (int64_t)nb * nd;
+    if (M * N > 0 && LL.nrow[Gp] > 0)
+      wsb += (int64_t)ns * (M + N) * slice_kp((int)LL.nrow[Gp]) * 2 + 8192;
+  }
+  uint8_t* cur = (uint8_t*)scratch((wsb + 7) / 8);
+  double fl = 0;
+  for (int gc = 0; gc < h; ++gc) {
+    const int gd = gc ^ G, Gp = ga ^ gc;
+    const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gd];
+    const int64_t M = (int64_t)na * nc, N = (int64_t)nb * nd;
+    const int64_t K = LL.nrow[Gp];
+    const int64_t c0 = coff;
+    coff += (int64_t)nc * nd;
+    if (M * N == 0 || K == 0) continue;
+    const int64_t ld = LL.ncol[Gp];
+    const double* A = L->d + LL.blk_off[Gp] + LL.csub[Gp * LL.ncode_c + ga] +
+                      (int64_t)b.a0 * nc;
+    const double* B = L->d + LL.blk_off[Gp] + LL.csub[Gp * LL.ncode_c + gb];
+    // both operands are K x (rows) blocks of L with leading dimension ld
+    if (M > ld || N > ld || (A - L->d) + (K - 1) * ld + M > LL.size ||
+        (B - L->d) + (K - 1) * ld + N > LL.size)
+      throw EngineError("internal: ladder build block out of bounds");
+    // op(A) rows (a,c) = columns of L (K-major slices of L^T), op(B)^T rows
+    // (b,d) likewise; both cached with L
+    TcProb& t = tp[np];
+    std::memset(&t, 0, sizeof(t));
+    t.a = slice_side(L, A, (int)M, (int)K, ld, 1, ns, false, &cur);
+    t.b = slice_side(L, B, (int)N, (int)K, ld, 1, ns, false, &cur);
+    t.M = (int)M;
+    t.N = (int)N;
+    t.K = (int)K;
+    t.ldc = (int)N;
+    TcLadEpi& e = ep[np];
+    e.W = lad_ws_;
+    e.rows = b.rows;
+    e.Kp = Kp;
+    e.coff = c0;
+    e.nc = nc;
+    e.nd = nd;
+    e.nb = nb;
+    e.ns = ns;
+    ++np;
+    fl += 2.0 * M * (double)N * K;
+  }
+  if (coff != ncol) throw EngineError("internal: ladder column count");
+  if (np > 0) {
+    tc_flops += (int64_t)fl;
+    timed(K_TC, fl, [&] {
+      return tc_gemm_ladder(tp, np, ns, ep, d_err, st_);
+    });
+  }
+  return fl;
+}
+
+// Y_G[(ij), (ab) in batch] += alpha * X_G[(ij),(cd)] W_batch^T with the
+// batch rows already in slices (lad_ws_)
+void Engine::ladder_apply_sliced(const LadBatch& b, double alpha, Tensor* X,
+                                 Tensor* Y, int ns) {
+  const Layout& XL = X->lay;
+  const int G = b.G;
+  const int64_t M = XL.nrow[G], K = XL.ncol[G];
+  if (M == 0) return;
+  const int gb = b.ga ^ G;
+  const double* A = X->d + XL.blk_off[G];
+  double* C = Y->d + Y->lay.blk_off[G] + Y->lay.csub[G * Y->lay.ncode_c + b.ga] +
+              (int64_t)b.a0 * dims_.n[SV][gb];
+  {
+    GemmProb g;
+    std::memset(&g, 0, sizeof(g));
+    g.A = A;
+    g.lda = (int)K;
+    g.B = nullptr;
+    g.C = C;
+    g.ldc = (int)K;
+    g.M = (int)M;
+    g.N = (int)b.rows;
+    g.K = (int)K;
+    // A and C inside their tensors (B is the slice buffer)
+    const int64_t ea = (A - X->d) + (M - 1) * K + K;
+    const int64_t ec = (C - Y->d) + (M - 1) * K + b.rows;
+    if (ea > XL.size || ec > Y->lay.size)
+      throw EngineError("internal: ladder apply out of bounds");
+  }
+  const int64_t Kp = slice_kp((int)K);
+  uint8_t* cur = (uint8_t*)scratch(
+      ((int64_t)ns * M * Kp * 2 + M * 4 + 8192 + 7) / 8);
+  TcProb t;
+  std::memset(&t, 0, sizeof(t));
+  t.a = slice_side(X, A, (int)M, (int)K, K, 0, ns, false, &cur);
+  t.b = {lad_ws_, nullptr, (int)b.rows, (int)Kp};
+  t.C = C;
+  t.M = (int)M;
+  t.N = (int)b.rows;
+  t.K = (int)K;
+  t.ldc = (int)K;
+  const double fl = 2.0 * M * (double)b.rows * K;
+  tc_flops += (int64_t)fl;
+  const int64_t sk = tc_sliced_scratch_doubles(&t, 1, ns);
+  double* skb = sk > 0 ? scratch(sk) : nullptr;
+  timed(K_TC, fl, [&] {
+    return tc_gemm_sliced(&t, 1, alpha, 1.0, ns, skb, d_err, st_);
+  });
+}
+
 // Y_G[(ij), (ab) in batch] += alpha * X_G[(ij),(cd)] W_batch^T
 void Engine::ladder_apply_batch(const LadBatch& b, double alpha, Tensor* X,
                                 Tensor* Y) {
@@ -303,9 +467,39 @@ void Engine::ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
     need = std::max(need, b.rows * T->lay.ncol[b.G]);
   ladder_reserve(need);
   double fl = 0;
+  const int ns = active_precision();
   for (const LadBatch& b : bs) {
-    fl += ladder_build(b, L);
-    ladder_apply_batch(b, alpha, T, R);
+    if (ladder_fusable(b, T->lay, L->lay)) {
+      // profiling: build and apply traced apart (keys outside "ladder*")
+      // (every trace record owns its two events: prof_collect returns
+      // both to the pool)
+      cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr, e3 = nullptr;
+      if (prof_on_) {
+        e0 = get_event();
+        cudaEventRecord(e0, st_);
+      }
+      const double fb = ladder_build_sliced(b, L, ns);
+      if (prof_on_) {
+        e1 = get_event();
+        e2 = get_event();
+        cudaEventRecord(e1, st_);
+        cudaEventRecord(e2, st_);
+      }
+      ladder_apply_sliced(b, alpha, T, R, ns);
+      if (prof_on_) {
+        e3 = get_event();
+        cudaEventRecord(e3, st_);
+        const double fa =
+            2.0 * (double)b.rows * T->lay.ncol[b.G] * T->lay.nrow[b.G];
+        trace_pending_.push_back({"part: fused ladder build [split]", e0, e1,
+                                  fb});
+        trace_pending_.push_back({"part: ladder apply [split]", e2, e3, fa});
+      }
+      fl += fb;
+    } else {
+      fl += ladder_build(b, L);
+      ladder_apply_batch(b, alpha, T, R);
+    }
     fl += 2.0 * (double)b.rows * T->lay.ncol[b.G] * T->lay.nrow[b.G];
     release_scratch();   // stream order: the next batch may reuse it
   }

@@ -14,10 +14,13 @@
 //     MMAs, tcgen05.commit frees smem stages; 4 warps drain the accumulator
 //     with tcgen05.ld and write FP64 (split-K partials go to scratch and are
 //     summed in a fixed order).
-// Tile: 128 rows (MMA M = 128, one CTA) x BN in {32, 64, 128} columns; the
-// larger output dimension is mapped to the 128-row side (C is then written
-// transposed).  Every mbarrier wait is bounded; on a timeout the kernel sets
-// an error flag, stops issuing work and still releases its tensor memory.
+// Tile: 128 rows (MMA M = 128) x BN in {32, 64, 128, 256} columns (MMA N =
+// BN); the larger output dimension is mapped to the 128-row side (C is then
+// written transposed).  The kernel is persistent (one CTA per SM walks its
+// tiles) with two TMEM accumulators, so one tile's epilogue overlaps the
+// next tile's loads and MMAs.  Every mbarrier wait is bounded; on a timeout
+// the kernel sets an error flag, stops issuing work, waits (bounded) for its
+// own copies in flight and still releases its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -29,6 +32,9 @@
 #include <stdexcept>
 #include <string>
 
+#include <cmath>
+
+#include "fp64_bits.cuh"
 #include "kernels.h"
 
 namespace cdcc {
@@ -37,7 +43,7 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;          // K per stage: one 128-byte swizzle row
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 192;    // TMA warp, MMA warp, 4 epilogue warps
 constexpr int TC_MAXPROB = 8;
 constexpr int TC_SMEM_BUDGET = 200 * 1024;
 constexpr long long TC_SPIN_LIMIT = 1LL << 22;
@@ -52,8 +58,12 @@ struct TcLaunch {
   int tile0[TC_MAXPROB + 1];
   int np, nslice, bn, stages, trans_out;
   double alpha, beta;
+  Pow2 ap2;                    // alpha as +-2^k (folded into the exponent)
   double* scratch;
   unsigned int* err;
+  // fused ladder epilogue: outputs go to BF16 slices of (ab|cd) rows
+  TcLadEpi lad[TC_MAXPROB];
+  int lad_on;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -156,6 +166,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+
+// Tile t of the launch -> problem, 128-row tile, column tile, K split.
+struct TcTile {
+  int pi, m0, n0, ksi, kb0, kb1;
+};
+
+__device__ __forceinline__ TcTile tc_tile(const TcLaunch& L, int t) {
+  TcTile r;
+  int pi = 0;
+  while (pi + 1 < L.np && t >= L.tile0[pi + 1]) ++pi;
+  int local = t - L.tile0[pi];
+  const int ksn = L.ks[pi];
+  r.pi = pi;
+  r.ksi = local % ksn;
+  local /= ksn;
+  r.n0 = (local % L.tn[pi]) * L.bn;
+  r.m0 = (local / L.tn[pi]) * TC_BM;
+  const int nkb = L.nkb[pi];
+  const int per = (nkb + ksn - 1) / ksn;
+  r.kb0 = r.ksi * per;
+  r.kb1 = min(nkb, r.kb0 + per);
+  if (r.kb1 < r.kb0) r.kb1 = r.kb0;
+  return r;
+}
+
+// Persistent and warp-specialised: CTA b takes tiles b, b + gridDim.x, ...
+// warp 0 issues the TMA loads of the K blocks into a ring of shared-memory
+// stages, warp 1 issues the MMAs of a tile into one of two TMEM accumulators
+// (alternating per tile), warps 2..5 drain the other accumulator (the
+// previous tile) and write its outputs, so the epilogue of one tile overlaps
+// the loads and MMAs of the next.  The three roles walk the same tile
+// sequence with running counters.
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ TcLaunch L) {
   extern __shared__ uint8_t smem_raw[];
@@ -165,33 +211,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t stage_bytes = (uint32_t)s * (a_bytes + b_bytes);
   uint64_t* full = (uint64_t*)(smem + (size_t)S * stage_bytes);
   uint64_t* empty = full + S;
-  uint64_t* done = empty + S;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* accf = empty + S;   // [2] accumulator ready
+  uint64_t* acce = accf + 2;    // [2] accumulator drained
+  uint64_t* fin = acce + 2;     // every MMA of this CTA complete
+  uint32_t* tmem_slot = (uint32_t*)(fin + 1);
+  int* consumed = (int*)(tmem_slot + 1);
+  double* stage_out = (double*)(smem + (size_t)S * stage_bytes + 256);
 
-  const int bid = blockIdx.x;
-  int pi = 0;
-  while (pi + 1 < L.np && bid >= L.tile0[pi + 1]) ++pi;
-  int local = bid - L.tile0[pi];
-  const int ksn = L.ks[pi];
-  const int ksi = local % ksn;
-  local /= ksn;
-  const int tn = local % L.tn[pi];
-  const int tm = local / L.tn[pi];
-  const int m0 = tm * TC_BM, n0 = tn * BN;
-  const int nkb = L.nkb[pi];
-  const int per = (nkb + ksn - 1) / ksn;
-  const int kb0 = ksi * per, kb1 = min(nkb, kb0 + per);
-  const int nit = max(0, kb1 - kb0);
-
+  const int ntile = L.tile0[L.np];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t ncols = BN < 32 ? 32 : (uint32_t)BN;
+  const uint32_t ncols = 2u * (uint32_t)BN;   // two accumulators
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    mbar_init(done, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], 4);   // one arrive per epilogue warp
+    }
+    mbar_init(fin, 1);
+    *consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -212,113 +253,248 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                          ((uint32_t)(BN >> 3) << 17) |
                          ((uint32_t)(TC_BM >> 4) << 24);
+  int issued = 0;
 
-  if (warp == 0 && lane == 0 && nit > 0) {
-    // ---- TMA producer
-    for (int it = 0; it < nit; ++it) {
-      const int st = it % S, round = it / S;
-      if (round > 0 && !mbar_wait(&empty[st], (round - 1) & 1, L.err, 1))
-        break;
-      mbar_expect_tx(&full[st], stage_bytes);
-      uint8_t* sa = smem + (size_t)st * stage_bytes;
-      uint8_t* sb = sa + (size_t)s * a_bytes;
-      const int kc = (kb0 + it) * TC_BK;
-      for (int i = 0; i < s; ++i) {
-        tma_load_3d(sa + (size_t)i * a_bytes, &L.ta[pi], kc, m0, i, &full[st]);
-        tma_load_3d(sb + (size_t)i * b_bytes, &L.tb[pi], kc, n0, i, &full[st]);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+        const TcTile T = tc_tile(L, t);
+        for (int kb = T.kb0; kb < T.kb1; ++kb, ++g) {
+          const int st = g % S, round = g / S;
+          if (round > 0 && !mbar_wait(&empty[st], (round - 1) & 1, L.err, 1)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[st], stage_bytes);
+          uint8_t* sa = smem + (size_t)st * stage_bytes;
+          uint8_t* sb = sa + (size_t)s * a_bytes;
+          const int kc = kb * TC_BK;
+          for (int i = 0; i < s; ++i) {
+            tma_load_3d(sa + (size_t)i * a_bytes, &L.ta[T.pi], kc, T.m0, i,
+                        &full[st]);
+            tma_load_3d(sb + (size_t)i * b_bytes, &L.tb[T.pi], kc, T.n0, i,
+                        &full[st]);
+          }
+          issued = g + 1;
+        }
       }
     }
-  } else if (warp == 1 && lane == 0 && nit > 0) {
-    // ---- MMA issuer
-    bool ok = true;
-    for (int it = 0; it < nit && ok; ++it) {
-      const int st = it % S, round = it / S;
-      if (!mbar_wait(&full[st], round & 1, L.err, 2)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
-      const uint32_t sb = sa + (uint32_t)s * a_bytes;
-      int first = (it == 0);
-      for (int d = 0; d < s; ++d)          // slice products i + j = d
-        for (int i = 0; i <= d; ++i) {
-          const int j = d - i;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: tile c (with K blocks) -> accumulator c & 1
+      bool ok = true;
+      int g = 0, c = 0;
+      for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+        const TcTile T = tc_tile(L, t);
+        if (T.kb1 <= T.kb0) continue;   // empty K split: no accumulator
+        const int set = c & 1;
+        if (c >= 2 && !mbar_wait(&acce[set], ((c >> 1) - 1) & 1, L.err, 4)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(set * BN);
+        int first = 1;
+        for (int kb = T.kb0; kb < T.kb1; ++kb, ++g) {
+          const int st = g % S, round = g / S;
+          if (!mbar_wait(&full[st], round & 1, L.err, 2)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(smem + (size_t)st * stage_bytes);
+          const uint32_t sb = sa + (uint32_t)s * a_bytes;
+          for (int d = 0; d < s; ++d)        // slice products i + j = d
+            for (int i = 0; i <= d; ++i) {
+              const int j = d - i;
 #pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk) {
-            const uint64_t ad = smem_desc(sa + i * a_bytes + kk * 32);
-            const uint64_t bd = smem_desc(sb + j * b_bytes + kk * 32);
-            mma_bf16(tmem, ad, bd, idesc, first ? 0u : 1u);
-            first = 0;
+              for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint64_t ad = smem_desc(sa + i * a_bytes + kk * 32);
+                const uint64_t bd = smem_desc(sb + j * b_bytes + kk * 32);
+                mma_bf16(acc, ad, bd, idesc, first ? 0u : 1u);
+                first = 0;
+              }
+            }
+          mma_commit(&empty[st]);
+          *(volatile int*)consumed = g + 1;
+        }
+        if (!ok) break;
+        mma_commit(&accf[set]);
+        ++c;
+      }
+      mma_commit(fin);   // arrives once every MMA issued above completed
+    }
+  } else {
+    // ---- epilogue warps 2..5: TMEM sub-partition warp % 4, 32 rows each.
+    // With the logical rows on the 128-row side (trans_out = 0) a lane
+    // holds one row of C; the warp passes 32 x 16 sub-tiles through shared
+    // memory so that consecutive lanes write consecutive columns.
+    const int sub = warp & 3;
+    double* stg = stage_out + sub * (32 * 17);
+    bool ok = true;
+    int c = 0;
+    for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+      const TcTile T = tc_tile(L, t);
+      const int pi = T.pi;
+      const bool have = T.kb1 > T.kb0;
+      const int set = c & 1;
+      if (have) {
+        if (!mbar_wait(&accf[set], (c >> 1) & 1, L.err, 3)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      }
+      const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
+      const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
+      double* C = L.C[pi];
+      const int ldc = L.ldc[pi];
+      const int ksn = L.ks[pi];
+      // logical C element (m, n) from the FP32 accumulator value v; FP64
+      // values are built with integer operations (fp64_bits.cuh)
+      auto put = [&](int m, int n, float v) {
+        if (L.lad_on) {
+          // X_gc[(a,c),(b,d)] -> row (a,b), column coff + c*nd + d of the
+          // batch's (ab|cd) rows, cut into BF16 slices hi + lo (+ ...)
+          const TcLadEpi& E = L.lad[pi];
+          const int a = m / E.nc, c = m - a * E.nc;
+          const int b = n / E.nd, d = n - b * E.nd;
+          const int64_t off = (int64_t)(a * E.nb + b) * E.Kp + E.coff +
+                              (int64_t)c * E.nd + d;
+          float w = v;
+#pragma unroll 1
+          for (int q = 0; q < E.ns; ++q) {
+            const __nv_bfloat16 hq = __float2bfloat16_rn(w);
+            ((__nv_bfloat16*)E.W)[(int64_t)q * E.rows * E.Kp + off] = hq;
+            w -= __bfloat162float(hq);
+          }
+          return;
+        }
+        if (ksn == 1) {
+          double* p = C + (int64_t)m * ldc + n;
+          double val;
+          if (L.ap2.ok) {
+            val = f32_to_f64_scaled(v, L.ap2.sh);
+            if (L.ap2.neg) val = -val;
+          } else {
+            val = L.alpha * f32_to_f64_scaled(v, 0);
+          }
+          if (L.beta == 0.0)
+            *p = val;
+          else if (L.beta == 1.0)
+            *p += val;
+          else
+            *p = fma(L.beta, *p, val);
+        } else {
+          L.scratch[L.poff[pi] + (int64_t)T.ksi * L.M[pi] * L.N[pi] +
+                    (int64_t)m * L.N[pi] + n] = f32_to_f64_scaled(v, 0);
+        }
+      };
+      float v[32];
+      float* stf = reinterpret_cast<float*>(stg);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (have) {
+          tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) +
+                        (uint32_t)(set * BN + c0),
+                    v);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = 0.f;
+        }
+        if (L.trans_out) {
+          // lanes run along n already
+          const int r = T.m0 + sub * 32 + lane;
+          if (r < Mr) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int cc = T.n0 + c0 + i;
+              if (cc >= Nc) break;
+              put(cc, r, v[i]);
+            }
+          }
+        } else if (L.lad_on) {
+          // fused ladder rows: the (a,c) part of each row's target offset
+          // is computed once per row (rbase), the (b,d) part once per
+          // column, so the 16 lanes of a row write 32 contiguous bytes
+          const TcLadEpi& E = L.lad[pi];
+          int64_t* rbase = reinterpret_cast<int64_t*>(
+              reinterpret_cast<char*>(stg) + 2304);
+          if (c0 == 0) {
+            __syncwarp();
+            const int m = T.m0 + sub * 32 + lane;
+            const int a = m / E.nc, c = m - a * E.nc;
+            rbase[lane] = (int64_t)a * E.nb * E.Kp + E.coff +
+                          (int64_t)c * E.nd;
+            __syncwarp();
+          }
+          __nv_bfloat16* W = (__nv_bfloat16*)E.W;
+          const int64_t sstride = E.rows * E.Kp;
+#pragma unroll
+          for (int h = 0; h < 32; h += 16) {
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) stf[lane * 17 + j] = v[h + j];
+            __syncwarp();
+            const int col = lane & 15;
+            const int n = T.n0 + c0 + h + col;
+            const int b = n / E.nd, d = n - b * E.nd;
+            const int64_t noff = (int64_t)b * E.Kp + d;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; rr += 2) {
+              const int row = rr + (lane >> 4);
+              const int m = T.m0 + sub * 32 + row;
+              if (m < Mr && n < Nc) {
+                const int64_t off = rbase[row] + noff;
+                float w = stf[row * 17 + col];
+#pragma unroll 1
+                for (int q = 0; q < E.ns; ++q) {
+                  const __nv_bfloat16 hq = __float2bfloat16_rn(w);
+                  W[(int64_t)q * sstride + off] = hq;
+                  w -= __bfloat162float(hq);
+                }
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int h = 0; h < 32; h += 16) {
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) stf[lane * 17 + j] = v[h + j];
+            __syncwarp();
+#pragma unroll 4
+            for (int rr = 0; rr < 32; rr += 2) {
+              const int row = rr + (lane >> 4), col = lane & 15;
+              const int m = T.m0 + sub * 32 + row, n = T.n0 + c0 + h + col;
+              if (m < Mr && n < Nc) put(m, n, stf[row * 17 + col]);
+            }
           }
         }
-      mma_commit(&empty[st]);
+      }
+      if (have) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[set]);
+        ++c;
+      }
     }
-    mma_commit(done);
   }
   __syncwarp();
-
-  // ---- epilogue: 4 warps x 32 TMEM lanes = 128 rows of the 128-row side.
-  // With the logical rows there (trans_out = 0) a lane holds one row of C;
-  // each warp then passes 32 x 16 sub-tiles through shared memory (the
-  // stage buffers are free once every MMA has completed) so that
-  // consecutive lanes write consecutive columns.
-  bool have = nit > 0;
-  if (have) have = mbar_wait(done, 0, L.err, 3);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
-  const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
-  double* C = L.C[pi];
-  const int ldc = L.ldc[pi];
-  auto put = [&](int m, int n, double dv) {   // logical C element (m, n)
-    if (ksn == 1) {
-      double* p = C + (int64_t)m * ldc + n;
-      const double val = L.alpha * dv;
-      *p = (L.beta == 0.0) ? val : fma(L.beta, *p, val);
-    } else {
-      L.scratch[L.poff[pi] + (int64_t)ksi * L.M[pi] * L.N[pi] +
-                (int64_t)m * L.N[pi] + n] = dv;
-    }
-  };
-  double* stg = reinterpret_cast<double*>(smem) + warp * (32 * 17);
-  float v[32];
-  for (int c0 = 0; c0 < BN; c0 += 32) {
-    if (have) {
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = 0.f;
-    }
-    if (L.trans_out) {
-      // lanes run along n already
-      const int r = m0 + warp * 32 + lane;
-      if (r < Mr) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int cc = n0 + c0 + i;
-          if (cc >= Nc) break;
-          put(cc, r, (double)v[i]);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int h = 0; h < 32; h += 16) {
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = (double)v[h + j];
-        __syncwarp();
-#pragma unroll 4
-        for (int rr = 0; rr < 32; rr += 2) {
-          const int row = rr + (lane >> 4), col = lane & 15;
-          const int m = m0 + warp * 32 + row, n = n0 + c0 + h + col;
-          if (m < Mr && n < Nc) put(m, n, stg[row * 17 + col]);
-        }
-      }
-    }
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (warp == 0 && lane == 0) {
+    // loads issued but never consumed (only after a timeout): wait for them
+    // to land before the CTA leaves (bounded)
+    for (int g = *(volatile int*)consumed; g < issued; ++g)
+      mbar_wait(&full[g % S], (g / S) & 1, L.err, 5);
+  }
   if (warp == 1) {
+    if (lane == 0) mbar_wait(fin, 0, L.err, 6);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
                      tmem),
                  "r"(ncols)
@@ -403,7 +579,10 @@ TcPlan tc_plan(const TcProb* p, int np, int s) {
   int maxc = 0;
   for (int i = 0; i < np; ++i)
     maxc = std::max(maxc, pl.swap ? p[i].M : p[i].N);
-  pl.bn = maxc <= 32 ? 32 : maxc <= 64 ? 64 : 128;
+  pl.bn = maxc <= 32 ? 32 : maxc <= 64 ? 64 : maxc <= 128 ? 128 : 256;
+  // at least two stages in flight: narrower column tiles otherwise
+  while (pl.bn > 32 && TC_SMEM_BUDGET / (s * (TC_BM * 128 + pl.bn * 128)) < 2)
+    pl.bn /= 2;
   const int stage = s * (TC_BM * 128 + pl.bn * 128);
   pl.stages = std::max(1, std::min(4, TC_SMEM_BUDGET / stage));
   int64_t tiles = 0;
@@ -488,13 +667,17 @@ int tc_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->trans_out = pl.swap ? 1 : 0;
   L->alpha = alpha;
   L->beta = beta;
+  L->ap2 = pow2_of(alpha);
   L->scratch = scratch;
   L->err = d_err;
   const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
-  const int smem = pl.stages * stage + 1024 + 256;
+  // stages, barriers, and four 32 x 17 double staging tiles for the output
+  const int smem = pl.stages * stage + 1024 + 256 + 4 * 32 * 17 * 8;
   cudaFuncSetAttribute(tc_gemm_kernel,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  tc_gemm_kernel<<<tiles, TC_THREADS, smem, st>>>(*L);
+  // persistent: one CTA per SM (at most one fits), tiles strided over them
+  const int grid = std::max(1, std::min(tiles, sm_count()));
+  tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(*L);
   delete L;
   int launches = 1;
   if (nr > 0) {
@@ -508,6 +691,55 @@ int tc_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
     ++launches;
   }
   return launches;
+}
+
+int tc_gemm_ladder(const TcProb* p, int np, int nslice, const TcLadEpi* epi,
+                   unsigned int* d_err, cudaStream_t st) {
+  if (np <= 0) return 0;
+  if (np > TC_MAXPROB) throw std::runtime_error("tc: too many blocks");
+  if (nslice < 1 || nslice > 3) throw std::runtime_error("tc: nslice");
+  TcPlan pl = tc_plan(p, np, nslice);
+  TcLaunch* L = new TcLaunch;
+  std::memset(L, 0, sizeof(TcLaunch));
+  int tiles = 0;
+  for (int i = 0; i < np; ++i) {
+    const TcProb& g = p[i];
+    const SlicedOp& rowop = pl.swap ? g.b : g.a;
+    const SlicedOp& colop = pl.swap ? g.a : g.b;
+    make_map(&L->ta[i], (const __nv_bfloat16*)rowop.data, rowop.Kp,
+             rowop.rows, nslice, TC_BM);
+    make_map(&L->tb[i], (const __nv_bfloat16*)colop.data, colop.Kp,
+             colop.rows, nslice, pl.bn);
+    L->C[i] = g.C;
+    L->M[i] = g.M;
+    L->N[i] = g.N;
+    L->ldc[i] = g.ldc;
+    L->nkb[i] = pl.nkb[i];
+    L->tm[i] = pl.tm[i];
+    L->tn[i] = pl.tn[i];
+    L->ks[i] = 1;               // whole K per tile: outputs go to slices
+    L->tile0[i] = tiles;
+    L->lad[i] = epi[i];
+    tiles += pl.tm[i] * pl.tn[i];
+  }
+  L->tile0[np] = tiles;
+  L->np = np;
+  L->nslice = nslice;
+  L->bn = pl.bn;
+  L->stages = pl.stages;
+  L->trans_out = pl.swap ? 1 : 0;
+  L->alpha = 1.0;
+  L->beta = 0.0;
+  L->err = d_err;
+  L->lad_on = 1;
+  const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
+  const int smem = pl.stages * stage + 1024 + 256 + 4 * 32 * 17 * 8;
+  cudaFuncSetAttribute(tc_gemm_kernel,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int grid = std::max(1, std::min(tiles, sm_count()));
+  tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(*L);
+  delete L;
+  return 1;
 }
 
 // ---- convenience: slice both operands of plain GemmProbs into `workspace`

@@ -33,6 +33,9 @@
 #include <stdexcept>
 #include <string>
 
+#include <cmath>
+
+#include "fp64_bits.cuh"
 #include "kernels.h"
 
 namespace cdcc {
@@ -58,6 +61,7 @@ struct OzLaunch {
   int tile0[OZ_MAXPROB + 1];
   int np, nslice, trans_out;
   double alpha, beta;
+  Pow2 ap2;                     // alpha as +-2^k (folded into the exponent)
   unsigned int* err;
 };
 
@@ -361,10 +365,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int er = r < Mr ? L.erow[pi][r] : 0;
       double* C = L.C[pi];
       const int ldc = L.ldc[pi];
-      auto put = [&](int m, int n, double val) {
+      // value 2^(sh) (hi + lo) as FP64: both halves converted with integer
+      // operations (scale folded into the exponent), one FP64 addition
+      const int ash = L.ap2.ok ? L.ap2.sh : 0;
+      auto value = [&](float h, float l, int sh) {
+        const double v = f32_to_f64_scaled(h, sh + ash) +
+                         f32_to_f64_scaled(l, sh + ash);
+        if (L.ap2.ok) return L.ap2.neg ? -v : v;
+        return L.alpha * v;
+      };
+      auto put = [&](int m, int n, double out) {
         double* p = C + (int64_t)m * ldc + n;
-        const double out = L.alpha * val;
-        *p = (L.beta == 0.0) ? out : fma(L.beta, *p, out);
+        if (L.beta == 0.0)
+          *p = out;
+        else if (L.beta == 1.0)
+          *p += out;
+        else
+          *p = fma(L.beta, *p, out);
       };
       if (L.trans_out) {
         if (r < Mr) {
@@ -372,8 +389,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int q = 0; q < OZ_BN; ++q) {
             const int cc = n0 + q;
             if (cc < Nc)
-              put(cc, r, ldexp((double)hi[q] + (double)lo[q],
-                               er + L.ecol[pi][cc]));
+              put(cc, r, value(hi[q], lo[q], er + L.ecol[pi][cc]));
           }
         }
       } else {
@@ -385,8 +401,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           for (int j = 0; j < 16; ++j) {
             const int cc = n0 + h + j;
             const int ec = cc < Nc ? L.ecol[pi][cc] : 0;
-            stg[lane * 17 + j] =
-                ldexp((double)hi[h + j] + (double)lo[h + j], er + ec);
+            stg[lane * 17 + j] = value(hi[h + j], lo[h + j], er + ec);
           }
           __syncwarp();
 #pragma unroll 4
@@ -497,6 +512,7 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->trans_out = swap ? 1 : 0;
   L->alpha = alpha;
   L->beta = beta;
+  L->ap2 = pow2_of(alpha);
   L->err = d_err;
   const int stage = nslice * (OZ_BM * 128 + OZ_BN * 128);
   // stages, barriers, and four 32 x 17 double staging tiles for the output

@@ -38,6 +38,12 @@ def declared_functions():
 def test_all_declared_symbols_exported(lib):
     names = declared_functions()
     assert "cd_ccsd_init" in names and "contract_dL" in names
+    # serving, error report and three-term gradient entry points
+    for n in ("cdcc_server_create", "cdcc_submit", "cdcc_poll", "cdcc_wait",
+              "cdcc_server_destroy", "cdcc_job_footprint",
+              "cdcc_energy_error", "contract_df", "cdcc_metric_size",
+              "cdcc_contract_dL_noalloc"):
+        assert n in names, n
     for n in names:
         assert hasattr(lib, n), n
 

@@ -110,3 +110,22 @@ def test_on_the_fly_ladder_tensor_core_schedules_c1(cd, prec):
     cd.cd_ccsd_free(ctx)
     assert abs(e - gold["e_corr"]) <= 1e-8
     assert np.abs(g - np.array(gold["gradient"])).max() <= 1e-6
+
+
+def test_fused_float_slice_ladder_with_empty_cholesky_irrep(cd):
+    # blocks large enough for the tensor-core route (the float-slice ladder
+    # builds its (ab|cd) batch rows straight into BF16 slices), an irrep
+    # without Cholesky vectors (zero integral blocks inside a batch) and
+    # small ragged row batches, in the tensor-core schedule against the
+    # FP64 oracle at the schedule's tolerance
+    s = random_system([5, 4, 4, 3], [24, 20, 20, 16], [40, 0, 34, 30],
+                      seed=214, scale=0.15)
+    dL = make_displacements(s, 3)
+    r = oracle_run(s)
+    G_or = pack_dense(s, r["G"].numpy())
+    for batch_gb in (0.0013, 2.0):
+        gg = run(cd, s, dL, ladder=cd.LADDER_OTF, ladder_batch_gb=batch_gb,
+                 precision=cd.PREC_TC, conv_tol=1e-10, energy_tol=1e-12)
+        assert gg["mode"] == cd.LADDER_OTF
+        assert abs(gg["e"] - r["cc"]["E_corr"]) <= 1e-8
+        assert np.abs(gg["g"] - dL @ G_or).max() <= 1e-6

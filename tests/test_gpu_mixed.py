@@ -37,7 +37,13 @@ def cd():
 
 SHAPES = [(1, 1, 1), (5, 3, 7), (128, 128, 64), (200, 37, 300),
           (32, 700, 650), (300, 290, 5000), (129, 257, 77), (64, 32, 1000),
-          (1, 1, 5000), (7, 9, 9000)]
+          (1, 1, 5000), (7, 9, 9000),
+          # one output side <= 16 (the narrow FP64 kernel): large M or large
+          # N, short K, long K split over CTAs, small sides 4, 8 and 16
+          (3000, 8, 8), (8, 3000, 68), (68, 8, 30000), (16, 700, 40),
+          (2000, 4, 100), (7, 1000, 20000), (300, 16, 1500),
+          # both sides <= 16 with the smaller one first, short K
+          (3, 10, 50), (10, 3, 50), (12, 16, 700)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
