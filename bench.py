@@ -87,6 +87,12 @@ def parse():
     ap.add_argument("--gemm-modes", default="0,2,14")
     ap.add_argument("--ref-blocks", type=int, default=1,
                     help="oracle ladder blocks timed per reference step")
+    ap.add_argument("--ladder-shape", action="store_true",
+                    help="two tensor-core CCSD iterations of a D2h system "
+                         "with the ladder batch shape of the o=60 v=540 "
+                         "nL=2400 workload (68 virtuals and 300 Cholesky "
+                         "vectors per irrep) but o=16: a small case for "
+                         "kernel captures")
     return ap.parse_args()
 
 
@@ -688,10 +694,41 @@ def run_gemm(args):
               f"{2.0 * M * N * K / best / 1e12:.2f} TFLOP/s", flush=True)
 
 
+def run_ladder_shape(args):
+    """Two tensor-core CCSD iterations (ladder on the fly) of a D2h system
+    whose ladder batches have the shape of the o=60 v=540 nL=2400 workload:
+    8 build products of 4624 x 4624 x 300 per batch, at a small device
+    footprint."""
+    import torch
+    from synth import random_system
+    from paper_2512_21909_gb300 import build as cbuild, cdcc
+    cbuild.build()
+    cdcc.load()
+    s = random_system([2] * 8, [68] * 8, [300] * 8, seed=5, scale=0.03)
+    o = cdcc.cdcc_default_options()
+    o.precision = cdcc.PREC_TC
+    o.max_iter = 2
+    o.ladder = cdcc.LADDER_OTF
+    ctx = cdcc.init_from_system(s, options=o)
+    try:
+        cdcc.ccsd_solve(ctx)
+    except cdcc.CdccError as err:
+        if err.status != cdcc.CDCC_ENOCONV:
+            raise
+    torch.cuda.synchronize()
+    print(json.dumps({"ladder_shape_case": "done",
+                      "peak_device_gb": torch.cuda.max_memory_allocated()
+                      / 1e9}))
+    cdcc.cd_ccsd_free(ctx)
+
+
 def main():
     args = parse()
     if args.gemm:
         run_gemm(args)
+        return
+    if args.ladder_shape:
+        run_ladder_shape(args)
         return
     rank, ws = dist_init()
     if args.impl == "reference":

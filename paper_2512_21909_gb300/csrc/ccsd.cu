@@ -98,6 +98,15 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Separable denominators of an amplitude layout for the Jacobi step.
+struct Denom2D {
+  Block2D* blocks = nullptr;
+  Chunk2D* chunks = nullptr;
+  double *rv = nullptr, *cv = nullptr;
+  int nblk = 0, nchunk = 0;
+  int64_t nrv = 0, ncv = 0;
+};
+
 struct Diis {
   int dim = 0, count = 0, next = 0;
   int64_t n = 0;
@@ -140,6 +149,7 @@ struct cdcc_ctx {
   Tensor *Gam = nullptr, *Gsym = nullptr, *D1a = nullptr, *D1s = nullptr;
   Tensor *Govov = nullptr, *Govvv = nullptr, *W0 = nullptr;
   Diis cc_diis, lam_diis;
+  Denom2D den[2];   // T1, T2 layouts
   unsigned int* d_err = nullptr;
   int iters_mixed[2] = {0, 0}, iters_fp64[2] = {0, 0};
   bool otf = false;   // ladder assembled on the fly (no stored W0)
@@ -366,19 +376,116 @@ double scalar(cdcc_ctx* c, const Tensor* t) {
   return v;
 }
 
+// Row and column parts of D = sum (occupied eps) - sum (virtual eps) for a
+// layout whose row group holds occupied and column group virtual indices
+// (t1: {SO,SV}/1, t2: {SO,SO,SV,SV}/2), with the row-major tuple order of
+// the DPD layout (dpd.h); rows are cut into chunks of ~16K elements.
+void build_denom(cdcc_ctx* c, const Layout& L, Denom2D& D) {
+  const Dims& d = c->dims;
+  const int h = d.h, nocc = c->hd.nocc;
+  const double* eps = c->eps.data();
+  std::vector<Block2D> blocks;
+  std::vector<Chunk2D> chunks;
+  std::vector<double> rv, cv;
+  auto group = [&](int q0, int m, int G, std::vector<double>& out) {
+    // tuples of irreps with xor G (g_0 slowest), then local indices
+    const int ncode = m >= 2 ? (m == 2 ? h : h * h) : 1;
+    for (int code = 0; code < ncode; ++code) {
+      int g[MAXRANK];
+      int x = G, cc = code;
+      for (int q = m - 2; q >= 0; --q) {
+        g[q] = cc % h;
+        cc /= h;
+        x ^= g[q];
+      }
+      g[m - 1] = x;
+      int64_t cnt = 1;
+      for (int q = 0; q < m; ++q) cnt *= d.n[L.sp[q0 + q]][g[q]];
+      for (int64_t e = 0; e < cnt; ++e) {
+        int64_t r = e;
+        double v = 0.0;
+        for (int q = m - 1; q >= 0; --q) {
+          const int sp = L.sp[q0 + q];
+          const int n = d.n[sp][g[q]];
+          const int l = (int)(r % n);
+          r /= n;
+          v += sp == SO ? eps[d.gstart[SO][g[q]] + l]
+                        : -eps[nocc + d.gstart[SV][g[q]] + l];
+        }
+        out.push_back(v);
+      }
+    }
+  };
+  for (int G = 0; G < h; ++G) {
+    Block2D b;
+    b.off = L.blk_off[G];
+    b.ncol = L.ncol[G];
+    b.rv0 = (int64_t)rv.size();
+    b.cv0 = (int64_t)cv.size();
+    group(0, L.split, G, rv);
+    group(L.split, L.rank - L.split, G ^ L.gtot, cv);
+    if ((int64_t)rv.size() - b.rv0 != L.nrow[G] ||
+        (int64_t)cv.size() - b.cv0 != L.ncol[G])
+      throw StatusError(CDCC_EINVAL, "internal: denominator layout");
+    const int blk = (int)blocks.size();
+    blocks.push_back(b);
+    if (L.nrow[G] == 0 || L.ncol[G] == 0) continue;
+    const int step = (int)std::max<int64_t>(
+        1, std::min<int64_t>(L.nrow[G], 16384 / std::max<int64_t>(1, L.ncol[G])));
+    for (int r = 0; r < L.nrow[G]; r += step)
+      chunks.push_back(
+          {blk, r, (int)std::min<int64_t>(step, L.nrow[G] - r)});
+  }
+  Engine& e = *c->eng;
+  D.nblk = (int)blocks.size();
+  D.nchunk = (int)chunks.size();
+  D.nrv = (int64_t)rv.size();
+  D.ncv = (int64_t)cv.size();
+  D.blocks = (Block2D*)e.al.alloc(blocks.size() * sizeof(Block2D));
+  D.chunks = (Chunk2D*)e.al.alloc(std::max<size_t>(1, chunks.size()) *
+                                  sizeof(Chunk2D));
+  D.rv = (double*)e.al.alloc(std::max<int64_t>(1, D.nrv) * 8);
+  D.cv = (double*)e.al.alloc(std::max<int64_t>(1, D.ncv) * 8);
+  CK(cudaMemcpyAsync(D.blocks, blocks.data(), blocks.size() * sizeof(Block2D),
+                     cudaMemcpyHostToDevice, c->st));
+  if (!chunks.empty())
+    CK(cudaMemcpyAsync(D.chunks, chunks.data(),
+                       chunks.size() * sizeof(Chunk2D),
+                       cudaMemcpyHostToDevice, c->st));
+  if (D.nrv)
+    CK(cudaMemcpyAsync(D.rv, rv.data(), D.nrv * 8, cudaMemcpyHostToDevice,
+                       c->st));
+  if (D.ncv)
+    CK(cudaMemcpyAsync(D.cv, cv.data(), D.ncv * 8, cudaMemcpyHostToDevice,
+                       c->st));
+  CK(cudaStreamSynchronize(c->st));   // host vectors go out of scope
+}
+
+void free_denom(cdcc_ctx* c, Denom2D& D) {
+  Engine& e = *c->eng;
+  if (D.blocks) e.al.release(D.blocks, D.nblk * sizeof(Block2D));
+  if (D.chunks)
+    e.al.release(D.chunks, std::max(1, D.nchunk) * sizeof(Chunk2D));
+  if (D.rv) e.al.release(D.rv, std::max<int64_t>(1, D.nrv) * 8);
+  if (D.cv) e.al.release(D.cv, std::max<int64_t>(1, D.ncv) * 8);
+  D = Denom2D();
+}
+
 // err = R / D over the amplitude vector layout; returns max |R/D|
 double probe_step(cdcc_ctx* c, Tensor* R1, Tensor* R2, Tensor* e1) {
   Engine& e = *c->eng;
   CK(cudaMemsetAsync(c->d_max, 0, 8, c->st));
-  const DevTasks& t1 = e.update_tasks(c->T1->lay);
-  const DevTasks& t2 = e.update_tasks(c->T2->lay);
+  if (!c->den[0].blocks) build_denom(c, c->T1->lay, c->den[0]);
+  if (!c->den[1].blocks) build_denom(c, c->T2->lay, c->den[1]);
+  const Denom2D &d1 = c->den[0], &d2 = c->den[1];
   const int64_t n1 = c->T1->lay.size;
+  // bytes: read R, write the step
   const double ub = 16.0 * (c->T1->lay.size + c->T2->lay.size);
   e.timed(Engine::K_UPDATE, ub, [&] {
-    return jacobi_update(t1.tasks, t1.chunks, t1.nchunk, R1->d, nullptr,
-                         e1->d, c->d_eps, c->d_max, c->st) +
-           jacobi_update(t2.tasks, t2.chunks, t2.nchunk, R2->d, nullptr,
-                         e1->d + n1, c->d_eps, c->d_max, c->st);
+    return jacobi2d(d1.blocks, d1.chunks, d1.nchunk, d1.rv, d1.cv, R1->d,
+                    nullptr, e1->d, c->d_max, c->st) +
+           jacobi2d(d2.blocks, d2.chunks, d2.nchunk, d2.rv, d2.cv, R2->d,
+                    nullptr, e1->d + n1, c->d_max, c->st);
   });
   unsigned long long bits = 0;
   CK(cudaMemcpyAsync(&bits, c->d_max, 8, cudaMemcpyDeviceToHost, c->st));
@@ -1279,6 +1386,8 @@ void free_ctx(cdcc_ctx* c) {
     e.al.release(c->d_dots, 16 * 8);
     e.al.release(c->d_partial, (size_t)c->partial_n * 8);
     e.al.release(c->d_err, 16);
+    free_denom(c, c->den[0]);
+    free_denom(c, c->den[1]);
     // optional per-contraction trace of the profiled work of this context
     if (const char* f = std::getenv("CDCC_TRACE")) e.write_trace(f);
     cudaStreamSynchronize(c->st);

@@ -130,6 +130,48 @@ __global__ void jacobi_kernel(const PermTask* __restrict__ tasks,
   }
 }
 
+// One CTA per chunk of rows; threads run along the row (coalesced), two
+// elements per thread per pass.
+__global__ void __launch_bounds__(256)
+    jacobi2d_kernel(const Block2D* __restrict__ blocks,
+                    const Chunk2D* __restrict__ chunks,
+                    const double* __restrict__ rv,
+                    const double* __restrict__ cv,
+                    const double* __restrict__ R, double* __restrict__ T,
+                    double* __restrict__ E, unsigned long long* maxbits) {
+  const Chunk2D ch = chunks[blockIdx.x];
+  const Block2D b = blocks[ch.blk];
+  double mx = 0.0;
+  for (int r = ch.row0; r < ch.row0 + ch.nrows; ++r) {
+    const double dr = rv[b.rv0 + r];
+    const int64_t base = b.off + (int64_t)r * b.ncol;
+    for (int64_t c = threadIdx.x; c < b.ncol; c += blockDim.x) {
+      const double D = dr + cv[b.cv0 + c];
+      const double s = R[base + c] / D;
+      if (T) T[base + c] += s;
+      if (E) E[base + c] = s;
+      mx = fmax(mx, fabs(s));
+      if (s != s) mx = __longlong_as_double(0x7ff8000000000000LL);
+    }
+  }
+  __shared__ unsigned long long red[32];
+  unsigned long long bb = dbl_bits(mx);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long ob = __shfl_down_sync(0xffffffffu, bb, o);
+    bb = ob > bb ? ob : bb;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bb;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    bb = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long ob = __shfl_down_sync(0xffffffffu, bb, o);
+      bb = ob > bb ? ob : bb;
+    }
+    if (threadIdx.x == 0) atomicMax(maxbits, bb);
+  }
+}
+
 struct PtrPack {
   const double* p[16];
   double c[16];
@@ -257,6 +299,15 @@ int jacobi_update(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
   if (nchunks <= 0) return 0;
   jacobi_kernel<<<nchunks, 256, 0, st>>>(d_tasks, d_chunks, R, t, err, eps,
                                          d_maxbits);
+  return 1;
+}
+
+int jacobi2d(const Block2D* d_blocks, const Chunk2D* d_chunks, int nchunks,
+             const double* rv, const double* cv, const double* R, double* t,
+             double* err, unsigned long long* d_maxbits, cudaStream_t st) {
+  if (nchunks <= 0) return 0;
+  jacobi2d_kernel<<<nchunks, 256, 0, st>>>(d_blocks, d_chunks, rv, cv, R, t,
+                                           err, d_maxbits);
   return 1;
 }
 

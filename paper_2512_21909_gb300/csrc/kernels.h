@@ -101,6 +101,22 @@ int jacobi_update(const PermTask* d_tasks, const Chunk* d_chunks, int nchunks,
                   const double* R, double* t, double* err, const double* eps,
                   unsigned long long* d_maxbits, cudaStream_t st);
 
+// Jacobi step on a block-diagonal amplitude layout with the denominator
+// separable per block, D[r,c] = rv[rv0 + r] + cv[cv0 + c] (row part: sum of
+// the occupied orbital energies of the row indices, column part: minus the
+// virtual ones): s = R / D, t += s (t may be null), err = s (may be null),
+// atomically max |s| into *d_maxbits.  Rows are swept contiguously; each
+// chunk is a run of rows of one block.
+struct Block2D {
+  int64_t off, ncol, rv0, cv0;
+};
+struct Chunk2D {
+  int blk, row0, nrows;
+};
+int jacobi2d(const Block2D* d_blocks, const Chunk2D* d_chunks, int nchunks,
+             const double* rv, const double* cv, const double* R, double* t,
+             double* err, unsigned long long* d_maxbits, cudaStream_t st);
+
 // out[k] = dot(xs[k], y) for k < m (m <= 16), deterministic two-pass.
 int multi_dot(const double* const* xs, int m, const double* y, int64_t n,
               double* d_partial, double* d_out, cudaStream_t st);

@@ -221,6 +221,8 @@ double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns) {
     ncol += (int64_t)dims_.n[SV][gc] * dims_.n[SV][gc ^ G];
   const int64_t Kp = slice_kp((int)ncol);
   const size_t need = (size_t)ns * b.rows * Kp * 2;
+  if ((int64_t)ns * b.rows * Kp >= ((int64_t)1 << 31))
+    throw EngineError("ladder batch too large for 32-bit slice offsets");
   if (need > lad_ws_bytes_) {
     if (lad_ws_) al.release(lad_ws_, lad_ws_bytes_);
     lad_ws_ = al.alloc(need);

@@ -43,7 +43,12 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;          // K per stage: one 128-byte swizzle row
-constexpr int TC_THREADS = 192;    // TMA warp, MMA warp, 4 epilogue warps
+// TMA warp, MMA warp, and 8 epilogue warps: two per TMEM sub-partition,
+// each draining half of a tile's columns (a single warp per scheduler left
+// the epilogue latency bound)
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr int TC_STG_BYTES = 2432;   // staging per epilogue warp
 constexpr int TC_MAXPROB = 8;
 constexpr int TC_SMEM_BUDGET = 200 * 1024;
 constexpr long long TC_SPIN_LIMIT = 1LL << 22;
@@ -202,6 +207,9 @@ __device__ __forceinline__ TcTile tc_tile(const TcLaunch& L, int t) {
 // previous tile) and write its outputs, so the epilogue of one tile overlaps
 // the loads and MMAs of the next.  The three roles walk the same tile
 // sequence with running counters.
+// LAD: the fused ladder epilogue (outputs to BF16 slices of (ab|cd) rows);
+// a separate instance so that each epilogue is compiled without the other
+template <bool LAD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ TcLaunch L) {
   extern __shared__ uint8_t smem_raw[];
@@ -216,7 +224,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* fin = acce + 2;     // every MMA of this CTA complete
   uint32_t* tmem_slot = (uint32_t*)(fin + 1);
   int* consumed = (int*)(tmem_slot + 1);
-  double* stage_out = (double*)(smem + (size_t)S * stage_bytes + 256);
+  // per epilogue warp TC_STG_BYTES of staging (a 32 x 17 float sub-tile,
+  // or for the fused ladder a 32 x 18 float sub-tile and 32 row offsets)
+  uint8_t* stage_out = smem + (size_t)S * stage_bytes + 256;
 
   const int ntile = L.tile0[L.np];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -229,7 +239,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accf[i], 1);
-      mbar_init(&acce[i], 4);   // one arrive per epilogue warp
+      mbar_init(&acce[i], TC_EPI_WARPS);   // one arrive per epilogue warp
     }
     mbar_init(fin, 1);
     *consumed = 0;
@@ -328,12 +338,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mma_commit(fin);   // arrives once every MMA issued above completed
     }
   } else {
-    // ---- epilogue warps 2..5: TMEM sub-partition warp % 4, 32 rows each.
-    // With the logical rows on the 128-row side (trans_out = 0) a lane
-    // holds one row of C; the warp passes 32 x 16 sub-tiles through shared
-    // memory so that consecutive lanes write consecutive columns.
+    // ---- epilogue warps 2..9: TMEM sub-partition warp % 4 (32 rows each),
+    // half (warp - 2) / 4 of the tile's columns.  With the logical rows on
+    // the 128-row side (trans_out = 0) a lane holds one row of C; the warp
+    // passes 32 x 16 sub-tiles through shared memory so that consecutive
+    // lanes write consecutive columns.
     const int sub = warp & 3;
-    double* stg = stage_out + sub * (32 * 17);
+    const int half = (warp - 2) >> 2;
+    float* stg = reinterpret_cast<float*>(stage_out +
+                                          (size_t)(warp - 2) * TC_STG_BYTES);
     bool ok = true;
     int c = 0;
     for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
@@ -356,7 +369,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // logical C element (m, n) from the FP32 accumulator value v; FP64
       // values are built with integer operations (fp64_bits.cuh)
       auto put = [&](int m, int n, float v) {
-        if (L.lad_on) {
+        if (LAD) {
           // X_gc[(a,c),(b,d)] -> row (a,b), column coff + c*nd + d of the
           // batch's (ab|cd) rows, cut into BF16 slices hi + lo (+ ...)
           const TcLadEpi& E = L.lad[pi];
@@ -394,8 +407,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       };
       float v[32];
-      float* stf = reinterpret_cast<float*>(stg);
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      float* stf = stg;
+      const int cbeg = half * (BN / 2), cend = BN < 64 ? (half ? 0 : BN)
+                                                       : cbeg + BN / 2;
+      for (int c0 = BN < 64 ? 0 : cbeg; c0 < cend; c0 += 32) {
+        __syncwarp();   // tcgen05.ld is warp-aligned
         if (have) {
           tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) +
                         (uint32_t)(set * BN + c0),
@@ -415,45 +431,89 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               put(cc, r, v[i]);
             }
           }
-        } else if (L.lad_on) {
-          // fused ladder rows: the (a,c) part of each row's target offset
-          // is computed once per row (rbase), the (b,d) part once per
-          // column, so the 16 lanes of a row write 32 contiguous bytes
+        } else if (LAD) {
+          // fused ladder rows.  Each 32 x 16 half of the warp's chunk is
+          // staged in shared memory; a lane then writes two adjacent columns
+          // of one row per step (8 lanes cover a row's 16 columns, 4 rows
+          // per step): the (a,c) part of a row's target offset is computed
+          // once per row, the (b,d) part once per half.  A pair inside one
+          // (b) group at an even offset is stored as one packed BF16 pair
+          // per slice, otherwise as two values (with nd odd the second
+          // column may start the next (b) group).
           const TcLadEpi& E = L.lad[pi];
-          int64_t* rbase = reinterpret_cast<int64_t*>(
-              reinterpret_cast<char*>(stg) + 2304);
-          if (c0 == 0) {
+          float* stc = stf;                                  // [32][18]
+          int32_t* rbase = reinterpret_cast<int32_t*>(stf + 32 * 18);
+          if (c0 == (BN < 64 ? 0 : cbeg)) {
             __syncwarp();
             const int m = T.m0 + sub * 32 + lane;
             const int a = m / E.nc, c = m - a * E.nc;
-            rbase[lane] = (int64_t)a * E.nb * E.Kp + E.coff +
-                          (int64_t)c * E.nd;
-            __syncwarp();
+            rbase[lane] = (int32_t)((int64_t)a * E.nb * E.Kp + E.coff +
+                                    (int64_t)c * E.nd);
           }
-          __nv_bfloat16* W = (__nv_bfloat16*)E.W;
-          const int64_t sstride = E.rows * E.Kp;
+          __nv_bfloat16* W0 = (__nv_bfloat16*)E.W;
+          const int32_t sstride = (int32_t)(E.rows * E.Kp);
+          __nv_bfloat16* W1 = W0 + sstride;
+          const int rows_ok = Mr - (T.m0 + sub * 32);
+          const int p2 = (lane & 7) * 2;             // column pair
+          const int rsel = lane >> 3;                // row within a step
 #pragma unroll
           for (int h = 0; h < 32; h += 16) {
             __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) stf[lane * 17 + j] = v[h + j];
+            for (int j = 0; j < 16; ++j) stc[lane * 18 + j] = v[h + j];
             __syncwarp();
-            const int col = lane & 15;
-            const int n = T.n0 + c0 + h + col;
-            const int b = n / E.nd, d = n - b * E.nd;
-            const int64_t noff = (int64_t)b * E.Kp + d;
+            const int n = T.n0 + c0 + h + p2;
+            const int nn = n < Nc ? n : Nc - 1;   // guarded below
+            const int b = nn / E.nd, d = nn - b * E.nd;
+            const int32_t noff = (int32_t)((int64_t)b * E.Kp + d);
+            // second column of the pair: same (b) group, or the first of
+            // the next one
+            const bool same = d + 1 < E.nd;
+            const int32_t noff1 =
+                same ? noff + 1 : (int32_t)((int64_t)(b + 1) * E.Kp);
+            const bool two = n + 1 < Nc;
+            if (E.ns == 2) {
 #pragma unroll 4
-            for (int rr = 0; rr < 32; rr += 2) {
-              const int row = rr + (lane >> 4);
-              const int m = T.m0 + sub * 32 + row;
-              if (m < Mr && n < Nc) {
-                const int64_t off = rbase[row] + noff;
-                float w = stf[row * 17 + col];
+              for (int rr = 0; rr < 32; rr += 4) {
+                const int row = rr + rsel;
+                if (row >= rows_ok || n >= Nc) continue;
+                const int32_t rb = rbase[row];
+                const int32_t off = rb + noff;
+                const float2 w = *reinterpret_cast<const float2*>(
+                    stc + row * 18 + p2);
+                const __nv_bfloat162 hi = __float22bfloat162_rn(w);
+                const float2 hf = __bfloat1622float2(hi);
+                const __nv_bfloat162 lo = __float22bfloat162_rn(
+                    make_float2(w.x - hf.x, w.y - hf.y));
+                if (two && same && !(off & 1)) {
+                  *reinterpret_cast<__nv_bfloat162*>(W0 + off) = hi;
+                  *reinterpret_cast<__nv_bfloat162*>(W1 + off) = lo;
+                } else {
+                  W0[off] = hi.x;
+                  W1[off] = lo.x;
+                  if (two) {
+                    const int32_t off1 = rb + noff1;
+                    W0[off1] = hi.y;
+                    W1[off1] = lo.y;
+                  }
+                }
+              }
+            } else {
+              for (int rr = 0; rr < 32; rr += 4) {
+                const int row = rr + rsel;
+                if (row >= rows_ok || n >= Nc) continue;
+                const int32_t rb = rbase[row];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                  if (k == 1 && !two) continue;
+                  const int32_t off = rb + (k == 0 ? noff : noff1);
+                  float w = stc[row * 18 + p2 + k];
 #pragma unroll 1
-                for (int q = 0; q < E.ns; ++q) {
-                  const __nv_bfloat16 hq = __float2bfloat16_rn(w);
-                  W[(int64_t)q * sstride + off] = hq;
-                  w -= __bfloat162float(hq);
+                  for (int q = 0; q < E.ns; ++q) {
+                    const __nv_bfloat16 hq = __float2bfloat16_rn(w);
+                    W0[q * sstride + off] = hq;
+                    w -= __bfloat162float(hq);
+                  }
                 }
               }
             }
@@ -672,12 +732,12 @@ int tc_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->err = d_err;
   const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
   // stages, barriers, and four 32 x 17 double staging tiles for the output
-  const int smem = pl.stages * stage + 1024 + 256 + 4 * 32 * 17 * 8;
-  cudaFuncSetAttribute(tc_gemm_kernel,
+  const int smem = pl.stages * stage + 1024 + 256 + TC_EPI_WARPS * TC_STG_BYTES;
+  cudaFuncSetAttribute(tc_gemm_kernel<false>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // persistent: one CTA per SM (at most one fits), tiles strided over them
   const int grid = std::max(1, std::min(tiles, sm_count()));
-  tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(*L);
+  tc_gemm_kernel<false><<<grid, TC_THREADS, smem, st>>>(*L);
   delete L;
   int launches = 1;
   if (nr > 0) {
@@ -733,11 +793,11 @@ int tc_gemm_ladder(const TcProb* p, int np, int nslice, const TcLadEpi* epi,
   L->err = d_err;
   L->lad_on = 1;
   const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
-  const int smem = pl.stages * stage + 1024 + 256 + 4 * 32 * 17 * 8;
-  cudaFuncSetAttribute(tc_gemm_kernel,
+  const int smem = pl.stages * stage + 1024 + 256 + TC_EPI_WARPS * TC_STG_BYTES;
+  cudaFuncSetAttribute(tc_gemm_kernel<true>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int grid = std::max(1, std::min(tiles, sm_count()));
-  tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(*L);
+  tc_gemm_kernel<true><<<grid, TC_THREADS, smem, st>>>(*L);
   delete L;
   return 1;
 }
