@@ -147,7 +147,7 @@ struct cdcc_ctx {
   Tensor *hoo, *hov, *hvo, *hvv, *Ioo;
   Tensor *amp, *T1, *T2, *res, *R1, *R2, *err1, *lam, *L1, *L2, *E;
   Tensor *Gam = nullptr, *Gsym = nullptr, *D1a = nullptr, *D1s = nullptr;
-  Tensor *Govov = nullptr, *Govvv = nullptr, *W0 = nullptr;
+  Tensor *Govov = nullptr, *Govvv = nullptr, *W0 = nullptr, *Xe = nullptr;
   Diis cc_diis, lam_diis;
   Denom2D den[2];   // T1, T2 layouts
   unsigned int* d_err = nullptr;
@@ -210,6 +210,11 @@ void prepare(cdcc_ctx* c) {
   e.contract(1.0, c->Lov, "Pmc", c->Lvv, "Pbd", 0.0, c->Govvv, "mcbd");
   c->Govov->symmetric = true;   // (ia|jb) is a symmetric matrix per block
   c->Govov->constant = c->Govvv->constant = true;
+  // 2 (ia|jb) - (ib|ja) of the energy expression, also amplitude independent
+  c->Xe = e.tensor("Xe", {SO, SV, SO, SV}, 2);
+  e.axpy(2.0, c->Govov, "iajb", 0.0, c->Xe, "iajb");
+  e.axpy(-1.0, c->Govov, "ibja", 1.0, c->Xe, "iajb");
+  c->Xe->constant = true;
   if (c->otf) return;           // the ladder builds its integrals itself
   c->W0 = e.tensor("W0", {SV, SV, SV, SV}, 2);
   e.contract(1.0, c->Lvv, "Pac", c->Lvv, "Pbd", 0.0, c->W0, "abcd");
@@ -363,10 +368,7 @@ void residual(cdcc_ctx* c) {
   Tensor* E = c->E;
   e.contract(1.0, hhoo, "kl", c->Ioo, "kl", 0.0, E, "");
   e.contract(1.0, Foo, "kl", c->Ioo, "kl", 1.0, E, "");
-  Tensor* Xe = T("Xe", {SO, SV, SO, SV}, 2);
-  e.axpy(2.0, Govov, "iajb", 0.0, Xe, "iajb");
-  e.axpy(-1.0, Govov, "ibja", 1.0, Xe, "iajb");
-  e.contract(1.0, Xe, "iajb", t2s, "ijab", 1.0, E, "");
+  e.contract(1.0, c->Xe, "iajb", t2s, "ijab", 1.0, E, "");
 }
 
 double scalar(cdcc_ctx* c, const Tensor* t) {
