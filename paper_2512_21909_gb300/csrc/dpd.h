@@ -84,10 +84,76 @@ struct PermTask {
   int dim[MAXRANK];
   int rank;
   int64_t n;       // elements in the box
+  // division by dim[q] as a multiply and shift, exact for numerators below
+  // 2^31: floor(r / dim[q]) = (r * mag[q]) >> shr[q] (set_division_magic)
+  uint64_t mag[MAXRANK];
+  int shr[MAXRANK];
+  // 1: n < 2^31 and every offset within the box (from ybase / xbase) is
+  // below 2^31, so the kernels index with 32-bit arithmetic
+  int off32;
   // global index bases for elementwise kernels that need orbital energies
   int gidx[MAXRANK];
   int sgn[MAXRANK];  // +1 occupied, -1 virtual, 0 unused
 };
+
+// Fill mag/shr/off32 of a task whose dim/ys/xs/rank/n are set.  With
+// l = ceil(log2 d), s = 31 + l and m = ceil(2^s / d), m d - 2^s < 2^l, so
+// floor(r m / 2^s) = floor(r / d) for every 0 <= r < 2^31 (Granlund and
+// Montgomery, "Division by invariant integers using multiplication",
+// PLDI 1994, Theorem 4.2); r m stays below 2^64.
+inline void set_division_magic(PermTask& t) {
+  int64_t yspan = 0, xspan = 0;
+  for (int q = 0; q < MAXRANK; ++q) {
+    const int64_t d = q < t.rank && t.dim[q] > 0 ? t.dim[q] : 1;
+    int l = 0;
+    while ((int64_t(1) << l) < d) ++l;
+    t.shr[q] = 31 + l;
+    t.mag[q] = ((uint64_t(1) << t.shr[q]) + (uint64_t)d - 1) / (uint64_t)d;
+    if (q < t.rank) {
+      yspan += (d - 1) * (t.ys[q] < 0 ? -t.ys[q] : t.ys[q]);
+      xspan += (d - 1) * (t.xs[q] < 0 ? -t.xs[q] : t.xs[q]);
+    }
+  }
+  t.off32 = (t.n < (int64_t(1) << 31) && yspan < (int64_t(1) << 31) &&
+             xspan < (int64_t(1) << 31))
+                ? 1
+                : 0;
+}
+
+// Merge neighbouring box dimensions q, q+1 that are contiguous in both
+// tensors (ys[q] = dim[q+1] ys[q+1], same for xs) and drop extents of 1;
+// the element order (row-major over the dims) is unchanged.  Only for tasks
+// that do not need the per-dimension indices (no orbital energies).
+inline void merge_box_dims(PermTask& t) {
+  int64_t dim[MAXRANK], ys[MAXRANK], xs[MAXRANK];
+  int r = 0;
+  for (int q = 0; q < t.rank; ++q) {
+    if (t.dim[q] == 1) continue;
+    if (r > 0 && ys[r - 1] == (int64_t)t.dim[q] * t.ys[q] &&
+        xs[r - 1] == (int64_t)t.dim[q] * t.xs[q] &&
+        dim[r - 1] * t.dim[q] <= INT32_MAX) {
+      dim[r - 1] *= t.dim[q];
+      ys[r - 1] = t.ys[q];
+      xs[r - 1] = t.xs[q];
+      continue;
+    }
+    dim[r] = t.dim[q];
+    ys[r] = t.ys[q];
+    xs[r] = t.xs[q];
+    ++r;
+  }
+  if (r == 0) {   // a single element
+    dim[0] = 1;
+    ys[0] = xs[0] = 0;
+    r = 1;
+  }
+  for (int q = 0; q < MAXRANK; ++q) {
+    t.dim[q] = q < r ? (int)dim[q] : 0;
+    t.ys[q] = q < r ? ys[q] : 0;
+    t.xs[q] = q < r ? xs[q] : 0;
+  }
+  t.rank = r;
+}
 
 struct Chunk {
   int task;

@@ -316,6 +316,8 @@ const DevTasks& Engine::perm_tasks(const Layout& Y, const Layout& X,
       }
       if (t.ybase < 0 || t.xbase < 0 || ymax >= Y.size || xmax >= X.size)
         throw EngineError("internal: permutation task out of bounds");
+      if (!eps) merge_box_dims(t);
+      set_division_magic(t);
       tasks.push_back(t);
     }
   });
@@ -324,6 +326,7 @@ const DevTasks& Engine::perm_tasks(const Layout& Y, const Layout& X,
     PermTask t;
     std::memset(&t, 0, sizeof(t));
     t.n = 1;
+    set_division_magic(t);
     tasks.push_back(t);
   }
   std::vector<Chunk> chunks;

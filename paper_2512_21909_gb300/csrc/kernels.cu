@@ -39,25 +39,38 @@ int sm_count() {
 // ----------------------------------------------------------- permute / axpy
 namespace {
 
-__device__ __forceinline__ void box_offsets(const PermTask& t, int64_t e,
-                                            int64_t& y, int64_t& x,
-                                            int* l) {
-  y = t.ybase;
-  x = t.xbase;
-  if (t.n <= 0x7fffffffLL) {
-    // 32-bit index arithmetic (every box below 2^31 elements)
-    int r = (int)e;
-    for (int q = t.rank - 1; q >= 0; --q) {
-      const int d = t.dim[q];
-      const int nq = r / d;
-      const int lq = r - nq * d;
+// Offsets (from ybase / xbase) and per-dimension indices of element e of a
+// box, 32-bit path (t.off32): the divisions by the extents are the
+// multiply-and-shift reciprocals of set_division_magic.  Unrolled over
+// MAXRANK so that the task's fields stay in registers; a rank-0 box (one
+// element) has zero strides.
+__device__ __forceinline__ void box_offsets32(const PermTask& t, int e,
+                                              int& y, int& x, int* l) {
+  y = 0;
+  x = 0;
+  uint32_t r = (uint32_t)e;
+#pragma unroll
+  for (int q = MAXRANK - 1; q > 0; --q) {
+    if (q < t.rank) {
+      const uint32_t nq = (uint32_t)(((uint64_t)r * t.mag[q]) >> t.shr[q]);
+      const int lq = (int)(r - nq * (uint32_t)t.dim[q]);
       r = nq;
       l[q] = lq;
-      y += (int64_t)lq * t.ys[q];
-      x += (int64_t)lq * t.xs[q];
+      y += lq * (int)t.ys[q];
+      x += lq * (int)t.xs[q];
     }
-    return;
   }
+  l[0] = (int)r;
+  y += (int)r * (int)t.ys[0];
+  x += (int)r * (int)t.xs[0];
+}
+
+// Same, 64-bit path (boxes or offsets of 2^31 elements and more).
+__device__ __forceinline__ void box_offsets64(const PermTask& t, int64_t e,
+                                              int64_t& y, int64_t& x,
+                                              int* l) {
+  y = 0;
+  x = 0;
   for (int q = t.rank - 1; q >= 0; --q) {
     const int d = t.dim[q];
     const int64_t lq = e % d;
@@ -68,21 +81,54 @@ __device__ __forceinline__ void box_offsets(const PermTask& t, int64_t e,
   }
 }
 
-__global__ void perm_axpy_kernel(const PermTask* __restrict__ tasks,
-                                 const Chunk* __restrict__ chunks,
-                                 double alpha, const double* __restrict__ X,
-                                 double beta, double* __restrict__ Y,
-                                 const double* __restrict__ dscale) {
+// Y = beta Y + alpha X over the chunk's elements.  Each thread takes PU
+// elements at a time (offsets first, then all loads, then the stores) so
+// that several loads are in flight per thread.
+constexpr int PU = 4;
+
+__global__ void __launch_bounds__(256)
+    perm_axpy_kernel(const PermTask* __restrict__ tasks,
+                     const Chunk* __restrict__ chunks, double alpha,
+                     const double* __restrict__ X, double beta,
+                     double* __restrict__ Y,
+                     const double* __restrict__ dscale) {
   const Chunk c = chunks[blockIdx.x];
-  const PermTask t = tasks[c.task];
+  const PermTask& t = tasks[c.task];
   const int64_t end = min(t.n, c.start + (int64_t)c.len);
   if (dscale) alpha *= *dscale;
   int l[MAXRANK];
+  const double* Xb = X + t.xbase;
+  double* Yb = Y + t.ybase;
+  if (t.off32) {
+    const int e1 = (int)end;
+    for (int e0 = (int)c.start + threadIdx.x; e0 < e1;
+         e0 += PU * blockDim.x) {
+      int yo[PU], xo[PU];
+      double v[PU];
+      bool in[PU];
+#pragma unroll
+      for (int u = 0; u < PU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        in[u] = e < e1;
+        yo[u] = xo[u] = 0;
+        if (in[u]) box_offsets32(t, e, yo[u], xo[u], l);
+      }
+#pragma unroll
+      for (int u = 0; u < PU; ++u) v[u] = in[u] ? alpha * Xb[xo[u]] : 0.0;
+#pragma unroll
+      for (int u = 0; u < PU; ++u) {
+        if (!in[u]) continue;
+        double* p = Yb + yo[u];
+        *p = (beta == 0.0) ? v[u] : fma(beta, *p, v[u]);
+      }
+    }
+    return;
+  }
   for (int64_t e = c.start + threadIdx.x; e < end; e += blockDim.x) {
     int64_t y, x;
-    box_offsets(t, e, y, x, l);
-    const double v = alpha * X[x];
-    Y[y] = (beta == 0.0) ? v : fma(beta, Y[y], v);
+    box_offsets64(t, e, y, x, l);
+    const double v = alpha * Xb[x];
+    Yb[y] = (beta == 0.0) ? v : fma(beta, Yb[y], v);
   }
 }
 
@@ -97,15 +143,26 @@ __global__ void jacobi_kernel(const PermTask* __restrict__ tasks,
                               const double* __restrict__ eps,
                               unsigned long long* maxbits) {
   const Chunk c = chunks[blockIdx.x];
-  const PermTask t = tasks[c.task];
+  const PermTask& t = tasks[c.task];
   const int64_t end = min(t.n, c.start + (int64_t)c.len);
   int l[MAXRANK];
   double mx = 0.0;
   for (int64_t e = c.start + threadIdx.x; e < end; e += blockDim.x) {
     int64_t y, x;
-    box_offsets(t, e, y, x, l);
+    if (t.off32) {
+      int y32, x32;
+      box_offsets32(t, (int)e, y32, x32, l);
+      y = t.ybase + y32;
+      x = t.xbase + x32;
+    } else {
+      box_offsets64(t, e, y, x, l);
+      y += t.ybase;
+      x += t.xbase;
+    }
     double D = 0.0;
-    for (int q = 0; q < t.rank; ++q) D += t.sgn[q] * eps[t.gidx[q] + l[q]];
+#pragma unroll
+    for (int q = 0; q < MAXRANK; ++q)
+      if (q < t.rank) D += t.sgn[q] * eps[t.gidx[q] + l[q]];
     const double s = R[y] / D;
     if (T) T[y] += s;
     if (E) E[y] = s;
@@ -386,13 +443,23 @@ __global__ void __launch_bounds__(256)
   const int64_t xrow = P.xoff[gc] + (int64_t)loc * len;
   const int64_t wbase = (int64_t)a * P.nb * P.ncol + P.coff[gc] +
                         (int64_t)c * nd;
+  if (len <= 0) return;
+  // (b, d) of element e walk forward by blockDim.x per step: one division
+  // per thread, then an add with carry
+  const int sb = blockDim.x / nd, sd = blockDim.x - sb * nd;
+  int b = threadIdx.x / nd, d = threadIdx.x - b * nd;
   for (int e = threadIdx.x; e < len; e += blockDim.x) {
-    const int b = e / nd, d = e - b * nd;
     const int64_t w = wbase + (int64_t)b * P.ncol + d;
     if (INV)
       dst[xrow + e] = src[w];
     else
       dst[w] = src[xrow + e];
+    b += sb;
+    d += sd;
+    if (d >= nd) {
+      d -= nd;
+      ++b;
+    }
   }
 }
 

@@ -11,13 +11,17 @@
 //     products with d < s.  Each P_d accumulates in its own FP32 tensor-
 //     memory accumulator and stays an exact integer below 2^24 for a K chunk
 //     of 192 (|terms| <= 2^16 for d = 0, <= 2^15 + 2^13 per k for d > 0).
-//   * after each chunk four drain warps read the s accumulators (tcgen05.ld)
-//     and add 2^(-16-7d) P_d into a per-thread double-float (hi, lo) FP32
-//     pair with error-free TwoSum, so the only rounding is the final
-//     2^-48-level one.  Two accumulator sets alternate so that the drain of
-//     chunk n overlaps the MMAs of chunk n+1.
+//   * after each chunk eight drain warps (two per TMEM sub-partition, each
+//     owning 32 of the 64 columns) read the s accumulators (tcgen05.ld) and
+//     add 2^(-16-7d) P_d into a per-thread double-float (hi, lo) FP32 pair
+//     with error-free TwoSum, so the only rounding is the final 2^-48-level
+//     one.  Two accumulator sets alternate so that the drain of chunk n
+//     overlaps the MMAs of chunk n+1; the second warp on each sub-partition
+//     computes while the first waits for its tensor-memory loads.
 // Operands are staged by TMA (128B swizzle) through a 2-stage pipeline; one
-// thread issues tcgen05.mma.kind::f16.  Tile: 128 rows x 64 columns (the
+// thread issues tcgen05.mma.kind::f16, s instructions per 16 of K (A_i
+// against the stacked B slices, N = (s - i) * 64) instead of one per slice
+// product.  Tile: 128 rows x 64 columns (the
 // larger output dimension on the 128-row side); the kernel is persistent
 // (one CTA per SM walks its tiles), so one tile's drain and write overlap
 // the next tile's loads and MMAs.  Every mbarrier wait is bounded and sets
@@ -44,7 +48,8 @@ namespace {
 
 constexpr int OZ_BM = 128, OZ_BN = 64, OZ_BK = 64;
 constexpr int OZ_KBLK_PER_CHUNK = 3;        // exact FP32 chunk: 192 of K
-constexpr int OZ_THREADS = 192;             // 6 warps
+constexpr int OZ_DRAIN_WARPS = 8;
+constexpr int OZ_THREADS = 64 + 32 * OZ_DRAIN_WARPS;   // 10 warps
 constexpr int OZ_MAXPROB = 8;
 constexpr int OZ_MAXS = 4;
 constexpr int OZ_STAGES = 2;
@@ -163,6 +168,42 @@ __device__ __forceinline__ void tld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// two 32-column loads (columns a.. and b..) behind one wait
+__device__ __forceinline__ void tld32x2(uint32_t ta, uint32_t tb, float* v,
+                                        float* w) {
+  uint32_t r[32], q[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, "
+      "[%65];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+        "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31]), "=r"(q[0]), "=r"(q[1]), "=r"(q[2]),
+        "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+        "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]),
+        "=r"(q[13]), "=r"(q[14]), "=r"(q[15]), "=r"(q[16]), "=r"(q[17]),
+        "=r"(q[18]), "=r"(q[19]), "=r"(q[20]), "=r"(q[21]), "=r"(q[22]),
+        "=r"(q[23]), "=r"(q[24]), "=r"(q[25]), "=r"(q[26]), "=r"(q[27]),
+        "=r"(q[28]), "=r"(q[29]), "=r"(q[30]), "=r"(q[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    v[i] = __uint_as_float(r[i]);
+    w[i] = __uint_as_float(q[i]);
+  }
+}
+
 // error-free (hi, lo) += v
 __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   const float s = hi + v;
@@ -200,7 +241,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   uint64_t* fin = acce + 2;             // all MMAs of this CTA complete
   uint32_t* tmem_slot = (uint32_t*)(fin + 1);
   int* consumed = (int*)(tmem_slot + 1);   // K blocks the MMA side used
-  // per drain warp a 32 x 16 staging tile for coalesced writes of C
+  // per drain warp a 32 x 16 staging tile (XOR-swizzled columns) for
+  // coalesced writes of C
   double* stage_out =
       (double*)(smem + (size_t)OZ_STAGES * stage_bytes + 256);
 
@@ -215,7 +257,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       bar_init(&accf[i], 1);
-      bar_init(&acce[i], 4);   // one arrive per drain warp
+      bar_init(&acce[i], OZ_DRAIN_WARPS);   // one arrive per drain warp
     }
     bar_init(fin, 1);
     *consumed = 0;
@@ -234,8 +276,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // F32 accumulate, BF16 A and B, both K-major, M = 128; N is or-ed in
+  // per instruction
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                         ((uint32_t)(OZ_BN >> 3) << 17) |
                          ((uint32_t)(OZ_BM >> 4) << 24);
   int issued = 0;   // producer: K blocks whose loads were issued
 
@@ -295,19 +338,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = su32(smem + (size_t)st * stage_bytes);
             const uint32_t sb = sa + (uint32_t)s * A_BYTES;
-            for (int d = 0; d < s; ++d) {
-              const uint32_t acc_addr =
-                  tmem + (uint32_t)((set * s + d) * OZ_BN);
-              int first = (kb == kb0);
-              for (int i = 0; i <= d; ++i) {
-                const int j = d - i;
+            // B_0 .. B_{s-1} lie back to back in the stage, i.e. one
+            // operand of s*64 rows: A_i times its first (s-i)*64 rows,
+            // written from column block i on, adds A_i B_j to block i+j = d
+            // for every j at once.  The i = 0 product covers all s blocks,
+            // so it alone starts a chunk's accumulation.
 #pragma unroll
-                for (int kk = 0; kk < OZ_BK / 16; ++kk) {
-                  umma(acc_addr, sdesc(sa + i * A_BYTES + kk * 32),
-                       sdesc(sb + j * B_BYTES + kk * 32), idesc,
-                       first ? 0u : 1u);
-                  first = 0;
-                }
+            for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+              for (int i = 0; i < s; ++i) {
+                const uint32_t acc_addr =
+                    tmem + (uint32_t)((set * s + i) * OZ_BN);
+                const uint32_t nn = (uint32_t)((s - i) * OZ_BN);
+                umma(acc_addr, sdesc(sa + i * A_BYTES + kk * 32),
+                     sdesc(sb + kk * 32), idesc | ((nn >> 3) << 17),
+                     (kb == kb0 && kk == 0 && i == 0) ? 0u : 1u);
               }
             }
             ucommit(&empty[st]);
@@ -320,17 +364,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       ucommit(fin);   // arrives once every MMA issued above has completed
     }
   } else {
-    // ---- drain warps 2..5: TMEM sub-partition (warp % 4), 32 rows each
+    // ---- drain warps 2..9: TMEM sub-partition (warp % 4), 32 rows each;
+    // warps 2..5 own columns 0..31 of the tile, warps 6..9 columns 32..63
+    constexpr int HW = OZ_BN / 2;
     const int sub = warp & 3;
+    const int half = (warp - 2) >> 2;
     bool ok = true;
     int c = 0;
     for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
       int pi, m0, n0;
       oz_tile(L, t, pi, m0, n0);
       const int nch = (L.nkb[pi] + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
-      float hi[OZ_BN], lo[OZ_BN];
+      float hi[HW], lo[HW];
 #pragma unroll
-      for (int i = 0; i < OZ_BN; ++i) hi[i] = lo[i] = 0.f;
+      for (int i = 0; i < HW; ++i) hi[i] = lo[i] = 0.f;
       for (int ch = 0; ch < nch; ++ch, ++c) {
         const int set = c & 1;
         if (!bar_wait(&accf[set], (c >> 1) & 1, L.err, 14)) {
@@ -338,17 +385,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int d = 0; d < s; ++d) {
+        const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) +
+                               (uint32_t)(set * s * OZ_BN + half * HW);
+        // s is 2, 3 or 4: accumulators d and d + 1 behind one wait
+        for (int d = 0; d < s; d += 2) {
+          float v[32], w[32];
+          const int d1 = d + 1 < s ? d + 1 : d;
+          tld32x2(tbase + (uint32_t)(d * OZ_BN),
+                  tbase + (uint32_t)(d1 * OZ_BN), v, w);
           const float sc = exp2f(-16.0f - 7.0f * d);
 #pragma unroll
-          for (int c0 = 0; c0 < OZ_BN; c0 += 32) {
-            float v[32];
-            tld32(tmem + ((uint32_t)(sub * 32) << 16) +
-                      (uint32_t)((set * s + d) * OZ_BN + c0),
-                  v);
+          for (int q = 0; q < 32; ++q) two_sum_add(hi[q], lo[q], v[q] * sc);
+          if (d1 != d) {
+            const float sc1 = sc * (1.0f / 128.0f);
 #pragma unroll
             for (int q = 0; q < 32; ++q)
-              two_sum_add(hi[c0 + q], lo[c0 + q], v[q] * sc);
+              two_sum_add(hi[q], lo[q], w[q] * sc1);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -356,10 +408,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (lane == 0) bar_arrive(&acce[set]);
       }
       if (!ok) break;
-      // ---- write: row r of the 128-row side, 64 columns.  With the
-      // logical rows on that side (trans_out = 0) the warp passes 32 x 16
+      // ---- write: row r of the 128-row side, this warp's 32 columns.  With
+      // the logical rows on that side (trans_out = 0) the warp passes 32 x 16
       // sub-tiles through shared memory so that lanes run along n.
       const int r = m0 + sub * 32 + lane;
+      const int nb = n0 + half * HW;
       const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
       const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
       const int er = r < Mr ? L.erow[pi][r] : 0;
@@ -386,29 +439,34 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       if (L.trans_out) {
         if (r < Mr) {
 #pragma unroll
-          for (int q = 0; q < OZ_BN; ++q) {
-            const int cc = n0 + q;
+          for (int q = 0; q < HW; ++q) {
+            const int cc = nb + q;
             if (cc < Nc)
               put(cc, r, value(hi[q], lo[q], er + L.ecol[pi][cc]));
           }
         }
       } else {
-        double* stg = stage_out + sub * (32 * 17);
+        // element (row, col) of the 32 x 16 tile sits at
+        // row * 16 + (col ^ (row & 15)): a row written by one lane and a
+        // row read by 16 lanes both touch 16 distinct bank pairs
+        double* stg = stage_out + (warp - 2) * (32 * 16);
 #pragma unroll
-        for (int h = 0; h < OZ_BN; h += 16) {
+        for (int h = 0; h < HW; h += 16) {
           __syncwarp();
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int cc = n0 + h + j;
+            const int cc = nb + h + j;
             const int ec = cc < Nc ? L.ecol[pi][cc] : 0;
-            stg[lane * 17 + j] = value(hi[h + j], lo[h + j], er + ec);
+            stg[lane * 16 + (j ^ (lane & 15))] =
+                value(hi[h + j], lo[h + j], er + ec);
           }
           __syncwarp();
 #pragma unroll 4
           for (int rr = 0; rr < 32; rr += 2) {
             const int row = rr + (lane >> 4), col = lane & 15;
-            const int m = m0 + sub * 32 + row, n = n0 + h + col;
-            if (m < Mr && n < Nc) put(m, n, stg[row * 17 + col]);
+            const int m = m0 + sub * 32 + row, n = nb + h + col;
+            if (m < Mr && n < Nc)
+              put(m, n, stg[row * 16 + (col ^ (row & 15))]);
           }
         }
       }
@@ -515,8 +573,8 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->ap2 = pow2_of(alpha);
   L->err = d_err;
   const int stage = nslice * (OZ_BM * 128 + OZ_BN * 128);
-  // stages, barriers, and four 32 x 17 double staging tiles for the output
-  const int smem = OZ_STAGES * stage + 1024 + 256 + 4 * 32 * 17 * 8;
+  // stages, barriers, and one 32 x 16 double staging tile per drain warp
+  const int smem = OZ_STAGES * stage + 1024 + 256 + OZ_DRAIN_WARPS * 32 * 16 * 8;
   cudaFuncSetAttribute(oz_gemm_kernel,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // persistent: one CTA per SM (at most one fits), tiles strided over them
