@@ -387,19 +387,20 @@ __global__ void __launch_bounds__(NR_ROWS)
   for (int64_t kb = k0; kb < k1; kb += NR_KC) {
     const int nk = (int)min((int64_t)NR_KC, k1 - kb);
     __syncthreads();
-    // large operand tile: 128 rows x 32 k, coalesced along the stored order
-    for (int e = t; e < NR_ROWS * NR_KC; e += NR_ROWS) {
+    // large operand tile: 128 rows x nk (<= 32) k, coalesced along the
+    // stored order; only the nk columns the FMAs below read are loaded
+    for (int e = t; e < NR_ROWS * nk; e += NR_ROWS) {
       int rr, kk;
       if (xk) {
-        rr = e / NR_KC;
-        kk = e - rr * NR_KC;
+        rr = e / nk;
+        kk = e - rr * nk;
       } else {
         kk = e / NR_ROWS;
         rr = e - kk * NR_ROWS;
       }
       const int r = r0 + rr;
       double v = 0.0;
-      if (r < R && kk < nk)
+      if (r < R)
         v = xk ? X[(int64_t)r * ldx + kb + kk] : X[(kb + kk) * ldx + r];
       xs[rr][kk] = v;
     }
@@ -426,6 +427,25 @@ __global__ void __launch_bounds__(NR_ROWS)
           if (q < S) acc[q] = fma(x, ys[kk][q], acc[q]);
       }
     }
+  }
+  if (bigA && T.ks[i] == 1) {
+    // rows of C (S <= 16 doubles each) are written through shared memory:
+    // consecutive threads take consecutive elements of the tile's rows
+    constexpr int OS = SB + 1;
+    double* os = &xs[0][0];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < SB; ++q)
+      if (q < S) os[t * OS + q] = acc[q];
+    __syncthreads();
+    const int rows = min(NR_ROWS, R - r0);
+    for (int e = t; e < rows * S; e += NR_ROWS) {
+      const int rr = e / S, q = e - rr * S;
+      double* c = P.C + (int64_t)(r0 + rr) * P.ldc + q;
+      const double v = T.alpha * os[rr * OS + q];
+      *c = (T.beta == 0.0) ? v : fma(T.beta, *c, v);
+    }
+    return;
   }
   const int r = r0 + t;
   if (r >= R) return;

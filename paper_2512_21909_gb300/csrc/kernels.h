@@ -54,8 +54,13 @@ int tc_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
                    int nslice, double* scratch, unsigned int* d_err,
                    cudaStream_t st);
 int64_t tc_sliced_scratch_doubles(const TcProb* p, int np, int nslice);
+// Exact-slice GEMM on pre-sliced operands; `scratch` holds
+// oz_sliced_scratch_doubles() doubles for the split-K partials (may be null
+// when that is 0).
+int64_t oz_sliced_scratch_doubles(const TcProb* p, int np);
 int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
-                   int nslice, unsigned int* d_err, cudaStream_t st);
+                   int nslice, double* scratch, unsigned int* d_err,
+                   cudaStream_t st);
 
 // Fused build of on-the-fly ladder rows (tc_gemm.cu): the product of
 // problem i is X_gc[(a,c),(b,d)] (a of the batch, M = na*nc, N = nb*nd) and
@@ -83,7 +88,8 @@ int tc_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
 
 // FP64-accurate tensor-core GEMM with exact integer slices (tc_ozaki.cu):
 // nslice in 2..4 (4: 29 bits of every element relative to its row /
-// column maximum).  `workspace` holds oz_workspace_bytes() bytes.
+// column maximum).  `workspace` holds oz_workspace_bytes() bytes (slices,
+// exponents and the split-K partials).
 int64_t oz_workspace_bytes(const GemmProb* p, int np, int nslice);
 int oz_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
                     int nslice, void* workspace, unsigned int* d_err,

@@ -890,8 +890,31 @@ int tc_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
                                    st);
 }
 
+namespace {
+// split-K partials of the exact-slice kernel for plain GemmProbs
+int64_t oz_scratch_doubles(const GemmProb* p, int np) {
+  TcProb t[TC_MAXPROB];
+  int n = 0;
+  for (int i = 0; i < np && n < TC_MAXPROB; ++i)
+    if (p[i].M > 0 && p[i].N > 0) {
+      std::memset(&t[n], 0, sizeof(TcProb));
+      t[n].M = p[i].M;
+      t[n].N = p[i].N;
+      t[n].K = p[i].K;
+      t[n].a.rows = p[i].M;
+      t[n].b.rows = p[i].N;
+      ++n;
+    }
+  return oz_sliced_scratch_doubles(t, n);
+}
+
+int64_t oz_slices_bytes(const GemmProb* p, int np, int nslice) {
+  return (sliced_workspace_bytes(p, np, nslice, true) + 1023) / 1024 * 1024;
+}
+}  // namespace
+
 int64_t oz_workspace_bytes(const GemmProb* p, int np, int nslice) {
-  return sliced_workspace_bytes(p, np, nslice, true);
+  return oz_slices_bytes(p, np, nslice) + 8 * oz_scratch_doubles(p, np);
 }
 
 int oz_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
@@ -901,7 +924,10 @@ int oz_gemm_grouped(const GemmProb* p, int np, double alpha, double beta,
   int launches = 0;
   const int n = prepare_sliced(p, np, nslice, true, workspace, t, st,
                                &launches);
-  return launches + oz_gemm_sliced(t, n, alpha, beta, nslice, d_err, st);
+  double* scratch =
+      (double*)((uint8_t*)workspace + oz_slices_bytes(p, np, nslice));
+  return launches +
+         oz_gemm_sliced(t, n, alpha, beta, nslice, scratch, d_err, st);
 }
 
 }  // namespace cdcc

@@ -63,11 +63,27 @@ struct OzLaunch {
   double* C[OZ_MAXPROB];
   int M[OZ_MAXPROB], N[OZ_MAXPROB], ldc[OZ_MAXPROB], nkb[OZ_MAXPROB];
   int tm[OZ_MAXPROB], tn[OZ_MAXPROB];
-  int tile0[OZ_MAXPROB + 1];
+  // split K: part kp of a tile takes the K blocks of chunks
+  // [kp * cps, (kp + 1) * cps) and writes its unscaled FP64 partial to
+  // scratch + poff + kp * M * N (logical row-major); oz_reduce_kernel adds
+  // the parts in order
+  int ks[OZ_MAXPROB], cps[OZ_MAXPROB];
+  int64_t poff[OZ_MAXPROB];
+  int tile0[OZ_MAXPROB + 1];   // counts (tile, part) pairs
   int np, nslice, trans_out;
   double alpha, beta;
   Pow2 ap2;                     // alpha as +-2^k (folded into the exponent)
+  double* scratch;
   unsigned int* err;
+};
+
+struct OzReduce {
+  double* C[OZ_MAXPROB];
+  int M[OZ_MAXPROB], N[OZ_MAXPROB], ldc[OZ_MAXPROB], ks[OZ_MAXPROB];
+  int64_t poff[OZ_MAXPROB], elem0[OZ_MAXPROB + 1];
+  int np;
+  double alpha, beta;
+  const double* scratch;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -213,14 +229,38 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   lo += e;
 }
 
-// Tile t of the launch -> (problem, 128-row tile, 64-column tile).
+// Work item t of the launch -> (problem, 128-row tile, 64-column tile,
+// K blocks [kb0, kb1) of its split part).
 __device__ __forceinline__ void oz_tile(const OzLaunch& L, int t, int& pi,
-                                        int& m0, int& n0) {
+                                        int& m0, int& n0, int& kp, int& kb0,
+                                        int& kb1) {
   pi = 0;
   while (pi + 1 < L.np && t >= L.tile0[pi + 1]) ++pi;
   const int local = t - L.tile0[pi];
-  m0 = (local / L.tn[pi]) * OZ_BM;
-  n0 = (local % L.tn[pi]) * OZ_BN;
+  const int tile = local / L.ks[pi];
+  kp = local - tile * L.ks[pi];
+  m0 = (tile / L.tn[pi]) * OZ_BM;
+  n0 = (tile % L.tn[pi]) * OZ_BN;
+  kb0 = min(L.nkb[pi], kp * L.cps[pi] * OZ_KBLK_PER_CHUNK);
+  kb1 = min(L.nkb[pi], kb0 + L.cps[pi] * OZ_KBLK_PER_CHUNK);
+}
+
+__global__ void oz_reduce_kernel(const __grid_constant__ OzReduce R) {
+  const int64_t total = R.elem0[R.np];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int pi = 0;
+    while (pi + 1 < R.np && e >= R.elem0[pi + 1]) ++pi;
+    const int64_t loc = e - R.elem0[pi];
+    const int m = (int)(loc / R.N[pi]), n = (int)(loc - (int64_t)m * R.N[pi]);
+    const int64_t MN = (int64_t)R.M[pi] * R.N[pi];
+    const double* part = R.scratch + R.poff[pi] + loc;
+    double acc = 0.0;
+    for (int k = 0; k < R.ks[pi]; ++k) acc += part[k * MN];
+    double* c = R.C[pi] + (int64_t)m * R.ldc[pi] + n;
+    const double v = R.alpha * acc;
+    *c = (R.beta == 0.0) ? v : fma(R.beta, *c, v);
+  }
 }
 
 // Persistent: CTA b takes tiles b, b + gridDim.x, ...  The three roles walk
@@ -288,9 +328,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       int g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
-        int pi, m0, n0;
-        oz_tile(L, t, pi, m0, n0);
-        for (int kb = 0; kb < L.nkb[pi]; ++kb, ++g) {
+        int pi, m0, n0, kp, kbb, kbe;
+        oz_tile(L, t, pi, m0, n0, kp, kbb, kbe);
+        for (int kb = kbb; kb < kbe; ++kb, ++g) {
           const int st = g % OZ_STAGES, round = g / OZ_STAGES;
           if (round > 0 && !bar_wait(&empty[st], (round - 1) & 1, L.err, 11)) {
             ok = false;
@@ -315,10 +355,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       bool ok = true;
       int g = 0, c = 0;
       for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
-        int pi, m0, n0;
-        oz_tile(L, t, pi, m0, n0);
-        const int nkb = L.nkb[pi];
-        const int nch = (nkb + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
+        int pi, m0, n0, kp, kbb, kbe;
+        oz_tile(L, t, pi, m0, n0, kp, kbb, kbe);
+        const int nch =
+            (kbe - kbb + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
         for (int ch = 0; ch < nch && ok; ++ch, ++c) {
           const int set = c & 1;
           if (c >= 2 &&
@@ -327,8 +367,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int kb0 = ch * OZ_KBLK_PER_CHUNK;
-          const int kb1 = min(nkb, kb0 + OZ_KBLK_PER_CHUNK);
+          const int kb0 = kbb + ch * OZ_KBLK_PER_CHUNK;
+          const int kb1 = min(kbe, kb0 + OZ_KBLK_PER_CHUNK);
           for (int kb = kb0; kb < kb1; ++kb, ++g) {
             const int st = g % OZ_STAGES, round = g / OZ_STAGES;
             if (!bar_wait(&full[st], round & 1, L.err, 13)) {
@@ -372,9 +412,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     bool ok = true;
     int c = 0;
     for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
-      int pi, m0, n0;
-      oz_tile(L, t, pi, m0, n0);
-      const int nch = (L.nkb[pi] + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
+      int pi, m0, n0, kp, kbb, kbe;
+      oz_tile(L, t, pi, m0, n0, kp, kbb, kbe);
+      const int nch = (kbe - kbb + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
       float hi[HW], lo[HW];
 #pragma unroll
       for (int i = 0; i < HW; ++i) hi[i] = lo[i] = 0.f;
@@ -416,20 +456,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const int Mr = L.trans_out ? L.N[pi] : L.M[pi];
       const int Nc = L.trans_out ? L.M[pi] : L.N[pi];
       const int er = r < Mr ? L.erow[pi][r] : 0;
-      double* C = L.C[pi];
-      const int ldc = L.ldc[pi];
+      // split K: the unscaled partial goes to this part's scratch slab
+      // (logical M x N, row-major; put() takes logical coordinates)
+      const bool part = L.ks[pi] > 1;
+      double* C = part ? L.scratch + L.poff[pi] +
+                             (int64_t)kp * L.M[pi] * L.N[pi]
+                       : L.C[pi];
+      const int ldc = part ? L.N[pi] : L.ldc[pi];
       // value 2^(sh) (hi + lo) as FP64: both halves converted with integer
       // operations (scale folded into the exponent), one FP64 addition
-      const int ash = L.ap2.ok ? L.ap2.sh : 0;
+      const int ash = (L.ap2.ok && !part) ? L.ap2.sh : 0;
       auto value = [&](float h, float l, int sh) {
         const double v = f32_to_f64_scaled(h, sh + ash) +
                          f32_to_f64_scaled(l, sh + ash);
+        if (part) return v;
         if (L.ap2.ok) return L.ap2.neg ? -v : v;
         return L.alpha * v;
       };
       auto put = [&](int m, int n, double out) {
         double* p = C + (int64_t)m * ldc + n;
-        if (L.beta == 0.0)
+        if (part || L.beta == 0.0)
           *p = out;
         else if (L.beta == 1.0)
           *p += out;
@@ -535,14 +581,68 @@ bool oz_swap(const TcProb* p, int np) {
 
 }  // namespace
 
+namespace {
+
+// Split-K plan: when the output tiles of all products cannot fill the SMs,
+// a product with at least four K chunks is cut into parts of whole chunks
+// (at least two per part), as many as fill the SMs.  Depends only on the
+// shapes and the SM count.
+struct OzPlan {
+  int ks[OZ_MAXPROB], cps[OZ_MAXPROB];
+  int64_t scratch;   // doubles
+};
+
+OzPlan oz_plan(const TcProb* p, int np) {
+  OzPlan pl;
+  std::memset(&pl, 0, sizeof(pl));
+  const bool swap = oz_swap(p, np);
+  int64_t tiles = 0;
+  for (int i = 0; i < np; ++i) {
+    const int rows = swap ? p[i].b.rows : p[i].a.rows;
+    const int cols = swap ? p[i].a.rows : p[i].b.rows;
+    tiles += (int64_t)((rows + OZ_BM - 1) / OZ_BM) * ((cols + OZ_BN - 1) / OZ_BN);
+  }
+  const int sms = sm_count();
+  for (int i = 0; i < np; ++i) {
+    const int nkb = (p[i].K + OZ_BK - 1) / OZ_BK;
+    const int nch = (nkb + OZ_KBLK_PER_CHUNK - 1) / OZ_KBLK_PER_CHUNK;
+    int ks = 1;
+    if (tiles > 0 && tiles < sms && nch >= 4) {
+      ks = (int)std::min<int64_t>((sms + tiles - 1) / tiles, nch / 2);
+      ks = std::max(1, std::min(ks, 64));
+    }
+    pl.cps[i] = ks > 1 ? (nch + ks - 1) / ks : std::max(nch, 1);
+    pl.ks[i] = ks > 1 ? (nch + pl.cps[i] - 1) / pl.cps[i] : 1;
+    if (pl.ks[i] > 1)
+      pl.scratch += (int64_t)pl.ks[i] * p[i].M * p[i].N;
+  }
+  return pl;
+}
+
+}  // namespace
+
+int64_t oz_sliced_scratch_doubles(const TcProb* p, int np) {
+  if (np <= 0) return 0;
+  if (np > OZ_MAXPROB) throw std::runtime_error("oz: too many blocks");
+  return oz_plan(p, np).scratch;
+}
+
 int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
-                   int nslice, unsigned int* d_err, cudaStream_t st) {
+                   int nslice, double* scratch, unsigned int* d_err,
+                   cudaStream_t st) {
   if (np <= 0) return 0;
   if (np > OZ_MAXPROB) throw std::runtime_error("oz: too many blocks");
   if (nslice < 2 || nslice > OZ_MAXS) throw std::runtime_error("oz: nslice");
   const bool swap = oz_swap(p, np);
+  const OzPlan pl = oz_plan(p, np);
+  if (pl.scratch > 0 && !scratch)
+    throw std::runtime_error("oz: split-K scratch missing");
   OzLaunch* L = new OzLaunch;
   std::memset(L, 0, sizeof(OzLaunch));
+  OzReduce R;
+  std::memset(&R, 0, sizeof(R));
+  int64_t poff = 0, relem = 0;
+  int nr = 0;
   int tiles = 0;
   for (int i = 0; i < np; ++i) {
     const TcProb& g = p[i];
@@ -561,8 +661,23 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
     L->nkb[i] = (g.K + OZ_BK - 1) / OZ_BK;
     L->tm[i] = (rowop.rows + OZ_BM - 1) / OZ_BM;
     L->tn[i] = (colop.rows + OZ_BN - 1) / OZ_BN;
+    L->ks[i] = pl.ks[i];
+    L->cps[i] = pl.cps[i];
+    L->poff[i] = pl.ks[i] > 1 ? poff : 0;
     L->tile0[i] = tiles;
-    tiles += L->tm[i] * L->tn[i];
+    tiles += L->tm[i] * L->tn[i] * L->ks[i];
+    if (pl.ks[i] > 1) {
+      R.C[nr] = g.C;
+      R.M[nr] = g.M;
+      R.N[nr] = g.N;
+      R.ldc[nr] = g.ldc;
+      R.ks[nr] = pl.ks[i];
+      R.poff[nr] = poff;
+      R.elem0[nr] = relem;
+      relem += (int64_t)g.M * g.N;
+      poff += (int64_t)pl.ks[i] * g.M * g.N;
+      ++nr;
+    }
   }
   L->tile0[np] = tiles;
   L->np = np;
@@ -571,6 +686,7 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->alpha = alpha;
   L->beta = beta;
   L->ap2 = pow2_of(alpha);
+  L->scratch = scratch;
   L->err = d_err;
   const int stage = nslice * (OZ_BM * 128 + OZ_BN * 128);
   // stages, barriers, and one 32 x 16 double staging tile per drain warp
@@ -578,13 +694,18 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   cudaFuncSetAttribute(oz_gemm_kernel,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // persistent: one CTA per SM (at most one fits), tiles strided over them
-  int dev = 0, sms = 148;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, std::min(tiles, sms));
+  const int grid = std::max(1, std::min(tiles, sm_count()));
   oz_gemm_kernel<<<grid, OZ_THREADS, smem, st>>>(*L);
   delete L;
-  return 1;
+  if (nr == 0) return 1;
+  R.np = nr;
+  R.elem0[nr] = relem;
+  R.alpha = alpha;
+  R.beta = beta;
+  R.scratch = scratch;
+  const int blocks = (int)std::min<int64_t>((relem + 255) / 256, 4096);
+  oz_reduce_kernel<<<std::max(blocks, 1), 256, 0, st>>>(R);
+  return 2;
 }
 
 }  // namespace cdcc

@@ -43,7 +43,10 @@ SHAPES = [(1, 1, 1), (5, 3, 7), (128, 128, 64), (200, 37, 300),
           (3000, 8, 8), (8, 3000, 68), (68, 8, 30000), (16, 700, 40),
           (2000, 4, 100), (7, 1000, 20000), (300, 16, 1500),
           # both sides <= 16 with the smaller one first, short K
-          (3, 10, 50), (10, 3, 50), (12, 16, 700)]
+          (3, 10, 50), (10, 3, 50), (12, 16, 700),
+          # small output, long K: the exact-slice kernel splits K over the
+          # SMs (fixed-order reduction of the parts)
+          (67, 67, 60000)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
