@@ -120,6 +120,12 @@ typedef struct {
                                convergence is accepted only on an iteration
                                with a fresh accurate anchor (default 1;
                                0 = every accurate iteration fully accurate) */
+    double perm_cache_gb;   /* device GB for permuted copies of the
+                               amplitude-independent tensors ((ia|jb),
+                               (mc|bd), L blocks) in the layouts their
+                               products need, made once per gradient and kept
+                               with their tensor-core slices (about 2.5x this
+                               in total); 0 = permute every time (default 32) */
 } cdcc_options;
 
 typedef struct cdcc_ctx cdcc_ctx;

@@ -41,7 +41,8 @@ class cdcc_options(ctypes.Structure):
                 ("alloc_user", ctypes.c_void_p), ("ladder", ctypes.c_int),
                 ("ladder_batch_gb", ctypes.c_double),
                 ("fock_model", ctypes.c_int),
-                ("ladder_linearize", ctypes.c_int)]
+                ("ladder_linearize", ctypes.c_int),
+                ("perm_cache_gb", ctypes.c_double)]
 
 
 class CdccError(RuntimeError):

@@ -206,8 +206,10 @@ void prepare(cdcc_ctx* c) {
   Engine& e = *c->eng;
   c->Govov = e.tensor("Govov", {SO, SV, SO, SV}, 2);
   e.contract(1.0, c->Lov, "Pia", c->Lov, "Pjb", 0.0, c->Govov, "iajb");
+  // (mc|bd) stored with rows (m,b) and columns (c,d): its products with
+  // the amplitudes (sums over c,d or over m,b) are then direct GEMMs
   c->Govvv = e.tensor("Govvv", {SO, SV, SV, SV}, 2);
-  e.contract(1.0, c->Lov, "Pmc", c->Lvv, "Pbd", 0.0, c->Govvv, "mcbd");
+  e.contract(1.0, c->Lov, "Pmc", c->Lvv, "Pbd", 0.0, c->Govvv, "mbcd");
   c->Govov->symmetric = true;   // (ia|jb) is a symmetric matrix per block
   c->Govov->constant = c->Govvv->constant = true;
   // 2 (ia|jb) - (ib|ja) of the energy expression, also amplitude independent
@@ -321,7 +323,7 @@ void residual(cdcc_ctx* c) {
   else
     e.ladder_stored(1.0, t2s, c->W0, Rr);                        // PPL
   Tensor* Yl = T("Ylad", {SO, SO, SO, SV}, 2);
-  e.contract(1.0, t2s, "ijcd", c->Govvv, "mcbd", 0.0, Yl, "ijmb");
+  e.contract(1.0, t2s, "ijcd", c->Govvv, "mbcd", 0.0, Yl, "ijmb");
   e.contract(-1.0, T1, "ma", Yl, "ijmb", 1.0, Rr, "ijab");
   e.contract(-1.0, T1, "nb", Yl, "jina", 1.0, Rr, "ijab");
   Tensor* Zl = T("Zlad", {SO, SO, SO, SO}, 2);
@@ -1198,6 +1200,12 @@ void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
   al.ff = c->opt.dev_free;
   al.user = c->opt.alloc_user;
   c->eng = std::make_unique<Engine>(d, c->st, al);
+  {
+    const double pc = c->opt.perm_cache_gb;
+    c->eng->set_perm_cache_bytes(pc > 0 && std::isfinite(pc)
+                                     ? (int64_t)(std::min(pc, 1e6) * 1e9)
+                                     : 0);
+  }
   Engine& e = *c->eng;
   CK(cudaEventCreate(&c->ev0));
   CK(cudaEventCreate(&c->ev1));
@@ -1420,6 +1428,7 @@ void cdcc_default_options(cdcc_options* o) {
   o->ladder_batch_gb = 2.0;
   o->fock_model = CDCC_FIXED_CORE;
   o->ladder_linearize = 1;
+  o->perm_cache_gb = 32.0;
 }
 
 cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,

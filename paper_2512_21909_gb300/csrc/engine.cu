@@ -178,6 +178,61 @@ cudaEvent_t Engine::get_event() {
   return e;
 }
 
+// Copy of constant tensor T (index string tl) in the matrix layout rows r,
+// columns c; null when the cache budget does not allow it.  With create =
+// false only reports whether the copy exists or would be made.
+Tensor* Engine::permuted_constant(Tensor* T, const std::string& tl,
+                                  const std::string& r, const std::string& c,
+                                  bool create) {
+  const std::string rc = r + c;
+  if ((int)rc.size() != T->lay.rank || (int)tl.size() != T->lay.rank)
+    return nullptr;
+  // the permutation as positions of the target letters in tl (letters are
+  // labels: "mcnd" -> "cdmn" and "kcld" -> "cdkl" are the same copy)
+  std::string key = T->name + '|';
+  std::vector<int> sp;
+  for (char x : rc) {
+    const size_t p = tl.find(x);
+    if (p == std::string::npos) return nullptr;
+    key += (char)('0' + (int)p);
+    sp.push_back(T->lay.sp[p]);
+  }
+  key += ':' + std::to_string(r.size());
+  auto it = perm_const_.find(key);
+  if (it != perm_const_.end()) {
+    if (create && it->second.src_ver != T->ver) {
+      Tensor* P = it->second.t;
+      axpy_raw(1.0, T->lay, T->d, tl, 0.0, P->lay, P->d, rc);
+      ++P->ver;
+      it->second.src_ver = T->ver;
+    }
+    return it->second.t;
+  }
+  const Layout L = make_layout(sp, (int)r.size(), T->lay.gtot);
+  const int64_t bytes = std::max<int64_t>(L.size, 1) * 8;
+  if (perm_const_cap_ <= 0 || perm_const_bytes_ + bytes > perm_const_cap_)
+    return nullptr;
+  if (!create) return T;   // would be made: any non-null answer
+  Tensor* P = new_tensor("perm:" + key, sp, (int)r.size(), T->lay.gtot);
+  P->constant = true;
+  P->ladder = T->ladder;
+  axpy_raw(1.0, T->lay, T->d, tl, 0.0, P->lay, P->d, rc);
+  P->ver = 1;
+  perm_const_[key] = {P, T->ver};
+  perm_const_bytes_ += bytes;
+  return P;
+}
+
+int Engine::sig_of(const std::string& s) {
+  auto it = sig_id_.find(s);
+  if (it != sig_id_.end()) return it->second;
+  const int id = (int)sig_name_.size();
+  sig_id_.emplace(s, id);
+  sig_name_.push_back(s);
+  sig_sec_.push_back({});
+  return id;
+}
+
 void Engine::prof_collect() {
   if (pending_.empty() && trace_pending_.empty()) return;
   ECK(cudaStreamSynchronize(st_));
@@ -185,6 +240,8 @@ void Engine::prof_collect() {
     float ms = 0;
     ECK(cudaEventElapsedTime(&ms, r.a, r.b));
     prof_sec[r.kind] += ms * 1e-3;
+    if (r.sig >= 0 && r.sig < (int)sig_sec_.size() && r.kind < 8)
+      sig_sec_[r.sig][r.kind] += ms * 1e-3;
     prof_work[r.kind] += r.work;
     prof_n[r.kind] += r.n;
     ev_pool_.push_back(r.a);
@@ -396,6 +453,7 @@ void Engine::axpy(double alpha, Tensor* X, const char* ix, double beta,
   if (recording_) tape_.push_back({1, alpha, beta, X, nullptr, Y, ix, "", iy});
   if (record_only_) return;
   ++Y->ver;
+  SigScope sig(this, std::string("axpy ") + ix + "->" + iy);
   axpy_raw(alpha, X->lay, X->d, ix, beta, Y->lay, Y->d, iy);
 }
 
@@ -410,6 +468,7 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
   if (recording_) tape_.push_back({0, alpha, beta, A, B, C, ia, ib, ic});
   if (record_only_) return;
   ++C->ver;
+  SigScope sig(this, ia + ',' + ib + "->" + ic);
   cudaEvent_t tr_a = nullptr;
   if (prof_on_) {
     tr_a = get_event();
@@ -475,6 +534,13 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
       throw EngineError("contract: index space mismatch");
   }
 
+  // a constant operand whose permuted copy is (or can be) kept costs
+  // nothing per call
+  auto perm_cost = [&](Tensor* T, const std::string& tl, const std::string& r,
+                       const std::string& c) -> int64_t {
+    if (T->constant && permuted_constant(T, tl, r, c, false)) return 0;
+    return T->lay.size;
+  };
   auto matches = [](const Tensor* T, const std::string& tl,
                     const std::string& r, const std::string& c, bool& tr) {
     if (tl == r + c && T->lay.split == (int)r.size()) {
@@ -510,8 +576,8 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
           const std::string& ql = form ? ia : ib;
           bool tr;
           int64_t cost = 0;
-          if (!matches(P, pl, X, K, tr)) cost += P->lay.size;
-          if (!matches(Q, ql, K, Y, tr)) cost += Q->lay.size;
+          if (!matches(P, pl, X, K, tr)) cost += perm_cost(P, pl, X, K);
+          if (!matches(Q, ql, K, Y, tr)) cost += perm_cost(Q, ql, K, Y);
           if (!(ic == X + Y && C->lay.split == (int)X.size()))
             cost += 2 * C->lay.size;
           if (best.cost < 0 || cost < best.cost) best = {form, K, X, Y, cost};
@@ -526,6 +592,10 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
                  const std::string& c) -> Mat {
     bool tr;
     if (matches(T, tl, r, c, tr)) return {T->d, &T->lay, tr, T};
+    if (T->constant) {
+      Tensor* Pc = permuted_constant(T, tl, r, c, true);
+      if (Pc) return {Pc->d, &Pc->lay, false, Pc};
+    }
     std::vector<int> sp;
     for (char x : r + c) sp.push_back(space_of(x));
     tmp_layouts_.push_back(std::make_unique<Layout>(
@@ -711,6 +781,25 @@ void Engine::write_trace(const char* file) {
                  (long long)a.calls, a.sec > 0 ? a.flops / a.sec / 1e12 : 0.0,
                  p.second.c_str());
   }
+  // device time of the launches issued for each signature, by class
+  static const char* kn[K_NKIND] = {"gemm64", "permute", "update", "dot",
+                                    "slice/other", "tc_float", "tc_exact"};
+  std::vector<std::pair<double, int>> w;
+  for (int i = 0; i < (int)sig_sec_.size(); ++i) {
+    double t = 0;
+    for (int k = 0; k < K_NKIND; ++k) t += sig_sec_[i][k];
+    w.push_back({t, i});
+  }
+  std::sort(w.rbegin(), w.rend());
+  std::fprintf(f, "# kernel classes per signature (device seconds)\n");
+  for (auto& p : w) {
+    if (p.first < 1e-4) break;
+    std::fprintf(f, "%10.6f s ", p.first);
+    for (int k = 0; k < K_NKIND; ++k)
+      if (sig_sec_[p.second][k] > 0)
+        std::fprintf(f, " %s %.4f", kn[k], sig_sec_[p.second][k]);
+    std::fprintf(f, "  | %s\n", sig_name_[p.second].c_str());
+  }
   std::fclose(f);
 }
 
@@ -793,8 +882,10 @@ void Engine::tc_contract(const GemmProb* probs, int np, const Mat& mp,
   }
   tc_flops += (int64_t)fl;
   if (exact) {
+    const int64_t sk = oz_sliced_scratch_doubles(tp, np);
+    double* skb = sk > 0 ? scratch(sk) : nullptr;
     timed(K_OZ, fl, [&] {
-      return oz_gemm_sliced(tp, np, alpha, beta, ns, d_err, st_);
+      return oz_gemm_sliced(tp, np, alpha, beta, ns, skb, d_err, st_);
     });
   } else {
     const int64_t sk = tc_sliced_scratch_doubles(tp, np, ns);

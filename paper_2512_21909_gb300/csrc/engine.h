@@ -15,6 +15,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <map>
 #include <memory>
 #include <set>
@@ -172,6 +173,8 @@ class Engine {
   enum ProfKind : int { K_GEMM64 = 0, K_PERM = 1, K_UPDATE = 2, K_DOT = 3,
                         K_OTHER = 4, K_TC = 5, K_OZ = 6, K_NKIND = 7 };
   void profile(bool on) { prof_on_ = on; }
+  // device bytes for permuted copies of constant tensors (0: none)
+  void set_perm_cache_bytes(int64_t b) { perm_const_cap_ = b; }
   template <class F>
   void timed(int kind, double work, F launch) {
     if (!prof_on_) {
@@ -183,7 +186,7 @@ class Engine {
     const int n = launch();
     cudaEventRecord(b, st_);
     launches += n;
-    pending_.push_back({kind, a, b, work, n});
+    pending_.push_back({kind, a, b, work, n, cur_sig_});
     if (pending_.size() > 8192) prof_collect();
   }
   void prof_collect();
@@ -309,6 +312,37 @@ class Engine {
     cudaEvent_t a, b;
     double work;
     int n;
+    int sig;   // contraction / permutation signature (-1: none)
+  };
+  // per-signature device time of each kernel class (profiling on): the
+  // signature of the contraction or permutation being issued
+  int cur_sig_ = -1;
+  std::map<std::string, int> sig_id_;
+  std::vector<std::string> sig_name_;
+  std::vector<std::array<double, 8>> sig_sec_;
+  int sig_of(const std::string& s);
+  // Permuted copies of amplitude-independent (constant) tensors, made once
+  // per version of the source and kept (their tensor-core slices are then
+  // cached with them): key = source name + position map + split.
+  struct PermConst {
+    Tensor* t;
+    uint64_t src_ver;
+  };
+  std::map<std::string, PermConst> perm_const_;
+  int64_t perm_const_bytes_ = 0;
+  int64_t perm_const_cap_ = int64_t(32) << 30;
+  Tensor* permuted_constant(Tensor* T, const std::string& tl,
+                            const std::string& r, const std::string& c,
+                            bool create);
+  // sets the signature for the launches issued in its scope (profiling on)
+  struct SigScope {
+    Engine* e;
+    int prev;
+    SigScope(Engine* eng, const std::string& s)
+        : e(eng), prev(eng->cur_sig_) {
+      if (eng->prof_on_) eng->cur_sig_ = eng->sig_of(s);
+    }
+    ~SigScope() { e->cur_sig_ = prev; }
   };
   cudaEvent_t get_event();
   bool prof_on_ = false;

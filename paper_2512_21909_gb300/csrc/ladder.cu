@@ -458,6 +458,7 @@ void Engine::ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
   Tensor* L = LW;
   Tensor* R = Y;
   ++R->ver;
+  SigScope sig(this, "ladder on the fly");
   cudaEvent_t tr_a = nullptr;
   if (prof_on_) {
     tr_a = get_event();
@@ -520,6 +521,7 @@ void Engine::ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
 void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
                             Tensor* dT, Tensor* dL) {
   if (!dT && !dL) return;
+  SigScope sig(this, "ladder on the fly, adjoint");
   cudaEvent_t tr_a = nullptr;
   if (prof_on_) {
     tr_a = get_event();

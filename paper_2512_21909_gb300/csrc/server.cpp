@@ -131,18 +131,20 @@ size_t packed_size(const std::vector<int>& n, const std::vector<int>& q,
 // estimate of its peak device memory.  About 64 doubles-sized arrays
 // (amplitudes, residuals, multipliers, two DIIS histories, the recorded
 // residual intermediates and their adjoints), (mc|bd) with its adjoint and
-// slices, L in its blocks with adjoint and slices, plus the ladder: stored
-// integrals with their adjoint and slices (16 / 28 / 36 bytes per element
-// for FP64 / MIXED / TC), or on the fly two batch buffers, the batch
-// slices and the adjoint batch slices of the density sweep (measured peaks
-// stay below five batches).
+// slices, L in its blocks with adjoint and slices, the permuted copies of
+// the constant tensors with their slices (about eight copies of o^2 v^2
+// size, 20 bytes per element, at most 2.5 x the cache budget), plus the
+// ladder: stored integrals with their adjoint and slices (16 / 28 / 36
+// bytes per element for FP64 / MIXED / TC), or on the fly two batch
+// buffers, the batch slices and the adjoint batch slices of the density
+// sweep (measured peaks stay below five batches).
 struct Footprint {
   int64_t t2 = 0, w = 0, ovvv = 0, nnz = 0;
   size_t bytes = 0, ladder_bytes = 0;
 };
 
 Footprint footprint(const cdcc_job_desc& j, int precision, int ladder,
-                    double batch_gb) {
+                    double batch_gb, double perm_gb) {
   Footprint f;
   std::vector<int> o, v, q;
   if (!counts(j, o, v, q)) return f;
@@ -155,8 +157,11 @@ Footprint footprint(const cdcc_job_desc& j, int precision, int ladder,
     f.ovvv += pairs(o, v, h, G) * pairs(v, v, h, G);
     f.nnz += (int64_t)q[G] * pairs(n, n, h, G);
   }
-  const double base =
-      8.0 * (64.0 * f.t2 + 4.0 * f.ovvv + 10.0 * f.nnz) + (512 << 20);
+  const double perm =
+      perm_gb > 0 ? std::min(8.0 * 20.0 * (double)f.t2, 2.5e9 * perm_gb)
+                  : 0.0;
+  const double base = 8.0 * (64.0 * f.t2 + 4.0 * f.ovvv + 10.0 * f.nnz) +
+                      perm + (512 << 20);
   double lad;
   if (ladder == CDCC_LADDER_STORED) {
     const double k = precision == CDCC_PREC_TC      ? 4.5
@@ -336,7 +341,9 @@ void cdcc_server_default_options(cdcc_server_options* s) {
 size_t cdcc_job_footprint(const cdcc_job_desc* job, int precision, int ladder,
                           double batch_gb) {
   if (!job || !job->orb_irrep || !job->chol_irrep) return 0;
-  return footprint(*job, precision, ladder, batch_gb).bytes;
+  cdcc_options d;
+  cdcc_default_options(&d);
+  return footprint(*job, precision, ladder, batch_gb, d.perm_cache_gb).bytes;
 }
 
 cdcc_status cdcc_server_create(cdcc_server** out, const cdcc_options* opt,
@@ -435,14 +442,17 @@ cdcc_status cdcc_submit(cdcc_server* s, const cdcc_job_desc* d,
     return CDCC_ECUDA;
   // ladder mode from the job's size only
   const Footprint fs =
-      footprint(j->desc(), s->opt.precision, CDCC_LADDER_STORED, 0.0);
+      footprint(j->desc(), s->opt.precision, CDCC_LADDER_STORED, 0.0,
+                s->opt.perm_cache_gb);
   j->ladder = (double)fs.ladder_bytes <= s->sopt.stored_max_gb * 1e9
                   ? CDCC_LADDER_STORED
                   : CDCC_LADDER_OTF;
   if (s->opt.ladder == CDCC_LADDER_STORED || s->opt.ladder == CDCC_LADDER_OTF)
     j->ladder = s->opt.ladder;
   const double bgb = s->opt.ladder_batch_gb > 0 ? s->opt.ladder_batch_gb : 2.0;
-  j->est_bytes = footprint(j->desc(), s->opt.precision, j->ladder, bgb).bytes;
+  j->est_bytes = footprint(j->desc(), s->opt.precision, j->ladder, bgb,
+                           s->opt.perm_cache_gb)
+                     .bytes;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stopping) return CDCC_ESTATE;
   j->ticket = s->next_ticket++;
