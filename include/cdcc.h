@@ -126,6 +126,13 @@ typedef struct {
                                products need, made once per gradient and kept
                                with their tensor-core slices (about 2.5x this
                                in total); 0 = permute every time (default 32) */
+    double ladder_slices_gb;/* ladder on the fly, float-slice arithmetic:
+                               GB of the (ab|cd) batch rows' BF16 slices
+                               kept from one ladder application to the next
+                               within a gradient (they depend on L only;
+                               kept while 8 GB stay free, freed before the
+                               density sweep); 0 = rebuild every
+                               application (default 48)                     */
 } cdcc_options;
 
 typedef struct cdcc_ctx cdcc_ctx;

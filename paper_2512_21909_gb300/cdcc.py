@@ -42,7 +42,8 @@ class cdcc_options(ctypes.Structure):
                 ("ladder_batch_gb", ctypes.c_double),
                 ("fock_model", ctypes.c_int),
                 ("ladder_linearize", ctypes.c_int),
-                ("perm_cache_gb", ctypes.c_double)]
+                ("perm_cache_gb", ctypes.c_double),
+                ("ladder_slices_gb", ctypes.c_double)]
 
 
 class CdccError(RuntimeError):

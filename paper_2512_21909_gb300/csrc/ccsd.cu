@@ -632,6 +632,8 @@ struct SwitchRule {
 };
 
 void check_device_error(cdcc_ctx* c) {
+  // launches outside Engine::timed report here at the latest
+  CK(cudaGetLastError());
   unsigned int err = 0;
   CK(cudaMemcpyAsync(&err, c->d_err, 4, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
@@ -653,6 +655,13 @@ bool linearised(cdcc_ctx* c) {
 void run_ccsd(cdcc_ctx* c, double* e_corr, int* iters, double* resid) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 0);
+  e.thaw();   // the forward tensors are written again
+  {
+    const double gb = c->opt.ladder_slices_gb;
+    e.ladder_keep_slices(gb > 0 && std::isfinite(gb)
+                             ? (int64_t)(std::min(gb, 1e6) * 1e9)
+                             : 0);
+  }
   c->fwd_fresh = false;
   c->res_acc = false;
   e.ladder_lin(0, 0);
@@ -742,6 +751,9 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 1);
   ensure_tape(c);
+  // every Lambda iteration (and the density sweep after it) reads the same
+  // forward tensors: their permuted copies and slices are kept meanwhile
+  e.freeze_tape_operands();
   e.zero(c->lam);
   e.set_precision(early_prec(c));
   bool early = mixed(c);
@@ -792,10 +804,13 @@ void frozen_fock_correction(cdcc_ctx* c);
 void run_density(cdcc_ctx* c, double* D1) {
   Engine& e = *c->eng;
   PhaseTimer pt(c, 2);
+  e.ladder_keep_slices(0);   // the sweep below builds its own batches
   ensure_tape(c);
+  e.freeze_tape_operands();
   e.set_precision(c->opt.precision == CDCC_PREC_TC ? 14 : (mixed(c) ? 3 : 0));
   e.backward({{c->E, nullptr}, {c->R1, c->L1}, {c->R2, c->L2}},
              TAG_L | TAG_H);
+  e.thaw();
   e.set_precision(0);
   assemble_density(c);
   if (c->opt.fock_model == CDCC_FROZEN_FOCK) frozen_fock_correction(c);
@@ -1059,6 +1074,7 @@ void run_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
                      cudaMemcpyDeviceToDevice, c->st));
   CK(cudaMemcpyAsync(keepD->d, c->D1s->d, (size_t)nd * 8,
                      cudaMemcpyDeviceToDevice, c->st));
+  e.thaw();
   ensure_tape(c);
   const int prec = e.precision();
   e.set_precision(0);
@@ -1108,6 +1124,7 @@ double lam_dot_res(cdcc_ctx* c) {
 // (each slice keeps 7 more bits of every operand).
 void run_energy_error(cdcc_ctx* c, double* dE) {
   Engine& e = *c->eng;
+  e.thaw();
   if (!c->res_acc) {
     // the accurate residual at t is needed again
     const int prec = e.precision();
@@ -1429,6 +1446,7 @@ void cdcc_default_options(cdcc_options* o) {
   o->fock_model = CDCC_FIXED_CORE;
   o->ladder_linearize = 1;
   o->perm_cache_gb = 32.0;
+  o->ladder_slices_gb = 48.0;
 }
 
 cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,

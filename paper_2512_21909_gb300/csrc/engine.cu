@@ -42,6 +42,15 @@ void DevAlloc::release(void* p, size_t bytes) {
     cudaFreeAsync(p, st);
 }
 
+bool device_free_above(size_t need, size_t reserve) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return fr > need + reserve;
+}
+
 Engine::Engine(const Dims& d, cudaStream_t st, DevAlloc a)
     : al(a), dims_(d), st_(st) {
   al.st = st;
@@ -60,6 +69,7 @@ Engine::~Engine() {
   if (lad_x_) al.release(lad_x_, (size_t)lad_n_ * 8);
   if (lad_w_) al.release(lad_w_, (size_t)lad_n_ * 8);
   if (lad_ws_) al.release(lad_ws_, lad_ws_bytes_);
+  for (auto& kv : lad_cache_) al.release(kv.second.data, kv.second.bytes);
   for (auto& kv : slice_cache_) {
     al.release(kv.second.data, kv.second.bytes);
     if (kv.second.exps) al.release(kv.second.exps, kv.second.ebytes);
@@ -213,12 +223,16 @@ Tensor* Engine::permuted_constant(Tensor* T, const std::string& tl,
   if (perm_const_cap_ <= 0 || perm_const_bytes_ + bytes > perm_const_cap_)
     return nullptr;
   if (!create) return T;   // would be made: any non-null answer
+  // a kept copy holds the same values as a per-call permutation, so it may
+  // depend on the free memory of the moment (8 GB stay free for the rest)
+  if (!device_free_above((size_t)bytes, (size_t)8 << 30)) return nullptr;
   Tensor* P = new_tensor("perm:" + key, sp, (int)r.size(), T->lay.gtot);
   P->constant = true;
+  P->frozen = T->frozen;   // its slices count against the frozen budget
   P->ladder = T->ladder;
   axpy_raw(1.0, T->lay, T->d, tl, 0.0, P->lay, P->d, rc);
   P->ver = 1;
-  perm_const_[key] = {P, T->ver};
+  perm_const_[key] = {P, T->ver, T};
   perm_const_bytes_ += bytes;
   return P;
 }
@@ -275,6 +289,61 @@ void Engine::set_precision(int slices) {
     if (kv.second.exps) al.release(kv.second.exps, kv.second.ebytes);
   }
   slice_cache_.clear();
+  frozen_slice_bytes_ = 0;
+}
+
+void Engine::freeze_tape_operands() {
+  for (const Op& op : tape_) {
+    for (Tensor* T : {op.A, op.B}) {
+      if (!T || T->constant || T->frozen) continue;
+      T->constant = true;
+      T->frozen = true;
+      frozen_.push_back(T);
+    }
+  }
+}
+
+void Engine::thaw() {
+  if (frozen_.empty()) return;
+  // drop the permuted copies of frozen tensors (and their slices)
+  std::set<const Tensor*> gone(frozen_.begin(), frozen_.end());
+  std::set<const Tensor*> copies;
+  for (auto it = perm_const_.begin(); it != perm_const_.end();) {
+    if (!gone.count(it->second.src)) {
+      ++it;
+      continue;
+    }
+    Tensor* P = it->second.t;
+    copies.insert(P);
+    perm_const_bytes_ -= std::max<int64_t>(P->lay.size, 1) * 8;
+    it = perm_const_.erase(it);
+  }
+  gone.insert(copies.begin(), copies.end());
+  ECK(cudaStreamSynchronize(st_));   // nothing in flight reads them
+  for (auto it = slice_cache_.begin(); it != slice_cache_.end();) {
+    if (!gone.count(it->second.owner)) {
+      ++it;
+      continue;
+    }
+    al.release(it->second.data, it->second.bytes);
+    if (it->second.exps) al.release(it->second.exps, it->second.ebytes);
+    it = slice_cache_.erase(it);
+  }
+  frozen_slice_bytes_ = 0;
+  for (auto it = tensors_.begin(); it != tensors_.end();) {
+    Tensor* t = it->second.get();
+    if (copies.count(t)) {
+      if (t->owns && t->d) al.release(t->d, (size_t)t->lay.size * 8);
+      it = tensors_.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (Tensor* T : frozen_) {
+    T->constant = false;
+    T->frozen = false;
+  }
+  frozen_.clear();
 }
 
 double* Engine::scratch(int64_t n) {
@@ -815,7 +884,19 @@ SlicedOp Engine::slice_side(Tensor* src, const double* ptr, int rows, int K,
                    : split_float(ptr, rows, K, ld, trans, nslice, d, st_);
     });
   };
-  if (src && src->constant) {
+  bool cache = src && src->constant;
+  if (cache && src->frozen) {
+    // frozen tensors: cached within their budget (entries are replaced
+    // in place when the key exists)
+    std::ostringstream k0;
+    k0 << (const void*)ptr << ':' << rows << ':' << K << ':' << ld << ':'
+       << trans << ':' << nslice << ':' << (exact ? 'x' : 'f');
+    if (!slice_cache_.count(k0.str()) &&
+        (frozen_slice_bytes_ + (int64_t)(bytes + ebytes) > frozen_slice_cap_ ||
+         !device_free_above(bytes + ebytes, (size_t)8 << 30)))
+      cache = false;
+  }
+  if (cache) {
     std::ostringstream key;
     key << (const void*)ptr << ':' << rows << ':' << K << ':' << ld << ':'
         << trans << ':' << nslice << ':' << (exact ? 'x' : 'f');
@@ -825,12 +906,16 @@ SlicedOp Engine::slice_side(Tensor* src, const double* ptr, int rows, int K,
     if (it != slice_cache_.end()) {
       al.release(it->second.data, it->second.bytes);
       if (it->second.exps) al.release(it->second.exps, it->second.ebytes);
+      if (it->second.owner && it->second.owner->frozen)
+        frozen_slice_bytes_ -= (int64_t)(it->second.bytes + it->second.ebytes);
       slice_cache_.erase(it);
     }
     SliceEntry en;
     en.bytes = bytes;
     en.ebytes = ebytes;
     en.ver = src->ver;
+    en.owner = src;
+    if (src->frozen) frozen_slice_bytes_ += (int64_t)(bytes + ebytes);
     en.data = al.alloc(bytes);
     en.exps = exact ? (int*)al.alloc(ebytes) : nullptr;
     split(en.data, en.exps);

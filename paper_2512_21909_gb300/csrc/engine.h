@@ -36,6 +36,9 @@ struct DevAlloc {
   void release(void* p, size_t bytes);
 };
 
+// more than need + reserve bytes of device memory free right now
+bool device_free_above(size_t need, size_t reserve);
+
 enum LeafTag : int { TAG_NONE = 0, TAG_AMP = 1, TAG_L = 2, TAG_H = 4 };
 
 struct Tensor {
@@ -56,6 +59,8 @@ struct Tensor {
   // operand of the particle-particle ladder ((ac|bd) integrals and their
   // adjoint): contractions touching it are timed as ladder work
   bool ladder = false;
+  // constant only while the adjoint sweeps run (Engine::freeze_tape_operands)
+  bool frozen = false;
   uint64_t ver = 0;   // bumped on every write
 };
 
@@ -173,17 +178,42 @@ class Engine {
   enum ProfKind : int { K_GEMM64 = 0, K_PERM = 1, K_UPDATE = 2, K_DOT = 3,
                         K_OTHER = 4, K_TC = 5, K_OZ = 6, K_NKIND = 7 };
   void profile(bool on) { prof_on_ = on; }
-  // device bytes for permuted copies of constant tensors (0: none)
-  void set_perm_cache_bytes(int64_t b) { perm_const_cap_ = b; }
+  // device bytes for permuted copies of constant tensors (0: none); the
+  // same budget again for the slices of frozen tensors
+  void set_perm_cache_bytes(int64_t b) {
+    perm_const_cap_ = b;
+    frozen_slice_cap_ = b;
+  }
+  // The operands of the recorded forward operations keep their values
+  // while adjoint sweeps of the tape run (the Lambda iterations and the
+  // density sweep write adjoints only): treat them as constant, so that
+  // their permuted copies and tensor-core slices are made once and reused
+  // by every sweep (within the cache budgets).  thaw() ends this and frees
+  // what was kept for them.
+  void freeze_tape_operands();
+  void thaw();
+  // keep up to `bytes` of on-the-fly ladder batch slices across ladder
+  // applications (0 frees them and stops keeping)
+  void ladder_keep_slices(int64_t bytes);
+  // a rejected launch (bad configuration, resources) is an error, never a
+  // silently missing result
+  static void check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+      throw EngineError(std::string("kernel launch: ") +
+                        cudaGetErrorString(e));
+  }
   template <class F>
   void timed(int kind, double work, F launch) {
     if (!prof_on_) {
       launches += launch();
+      check_launch();
       return;
     }
     cudaEvent_t a = get_event(), b = get_event();
     cudaEventRecord(a, st_);
     const int n = launch();
+    check_launch();
     cudaEventRecord(b, st_);
     launches += n;
     pending_.push_back({kind, a, b, work, n, cur_sig_});
@@ -219,7 +249,11 @@ class Engine {
     int* exps;
     size_t bytes, ebytes;
     uint64_t ver;
+    const Tensor* owner;
   };
+  int64_t frozen_slice_bytes_ = 0;
+  int64_t frozen_slice_cap_ = int64_t(32) << 30;
+  std::vector<Tensor*> frozen_;
   std::map<std::string, SliceEntry> slice_cache_;
   // contraction trace (profiling on): signature -> events
   struct TraceRec {
@@ -254,11 +288,24 @@ class Engine {
   // batch rows directly (lad_ws_) and the apply reads them; false when a
   // block is too small for the tensor-core route
   bool ladder_fusable(const LadBatch& b, const Layout& TL, const Layout& LL);
-  double ladder_build_sliced(const LadBatch& b, Tensor* L, int ns);
+  // into dst (ns * rows * Kp BF16; null: the batch buffer lad_ws_)
+  double ladder_build_sliced(const LadBatch& b, Tensor* L, int ns,
+                             void* dst = nullptr);
   void ladder_apply_sliced(const LadBatch& b, double alpha, Tensor* X,
-                           Tensor* Y, int ns);
+                           Tensor* Y, int ns, const void* W = nullptr);
   void* lad_ws_ = nullptr;
   size_t lad_ws_bytes_ = 0;
+  // BF16 slices of the on-the-fly batch rows kept across ladder
+  // applications (float-slice arithmetic; they depend on L only): key
+  // "G,ga,a0,a1,ns" -> buffer, valid for one version of L
+  struct LadSlices {
+    void* data;
+    size_t bytes;
+    uint64_t lver;
+    const Tensor* L;
+  };
+  std::map<std::string, LadSlices> lad_cache_;
+  int64_t lad_cache_bytes_ = 0, lad_cache_cap_ = 0;
   void ladder_perm(const LadBatch& b, bool inverse, const double* src,
                    double* dst);
   void ladder_apply_batch(const LadBatch& b, double alpha, Tensor* X,
@@ -327,6 +374,7 @@ class Engine {
   struct PermConst {
     Tensor* t;
     uint64_t src_ver;
+    const Tensor* src;
   };
   std::map<std::string, PermConst> perm_const_;
   int64_t perm_const_bytes_ = 0;

@@ -212,7 +212,8 @@ bool Engine::ladder_fusable(const LadBatch& b, const Layout& TL,
 
 // Batch rows of (ab|cd) as ns BF16 slices [ns][rows][Kp] (lad_ws_), written
 // by the epilogue of the build GEMM; returns its flops.
-double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns) {
+double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns,
+                                   void* dst) {
   const int h = dims_.h, G = b.G, ga = b.ga, gb = ga ^ G;
   const int na = b.a1 - b.a0, nb = dims_.n[SV][gb];
   const Layout& LL = L->lay;
@@ -223,11 +224,12 @@ double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns) {
   const size_t need = (size_t)ns * b.rows * Kp * 2;
   if ((int64_t)ns * b.rows * Kp >= ((int64_t)1 << 31))
     throw EngineError("ladder batch too large for 32-bit slice offsets");
-  if (need > lad_ws_bytes_) {
+  if (!dst && need > lad_ws_bytes_) {
     if (lad_ws_) al.release(lad_ws_, lad_ws_bytes_);
     lad_ws_ = al.alloc(need);
     lad_ws_bytes_ = need;
   }
+  void* W = dst ? dst : lad_ws_;
   // zero padding columns [ncol, Kp) and, for an irrep without Cholesky
   // vectors, the whole batch ((ac|bd) = 0 there)
   bool holes = false;
@@ -237,9 +239,9 @@ double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns) {
     if (M * N > 0 && LL.nrow[ga ^ gc] == 0) holes = true;
   }
   if (holes)
-    LCK(cudaMemsetAsync(lad_ws_, 0, need, st_));
+    LCK(cudaMemsetAsync(W, 0, need, st_));
   else if (Kp > ncol)
-    LCK(cudaMemset2DAsync((uint8_t*)lad_ws_ + ncol * 2, (size_t)Kp * 2, 0,
+    LCK(cudaMemset2DAsync((uint8_t*)W + ncol * 2, (size_t)Kp * 2, 0,
                           (size_t)(Kp - ncol) * 2, (size_t)ns * b.rows, st_));
   TcProb tp[GEMM_MAXPROB];
   TcLadEpi ep[GEMM_MAXPROB];
@@ -281,7 +283,7 @@ double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns) {
     t.K = (int)K;
     t.ldc = (int)N;
     TcLadEpi& e = ep[np];
-    e.W = lad_ws_;
+    e.W = W;
     e.rows = b.rows;
     e.Kp = Kp;
     e.coff = c0;
@@ -305,7 +307,7 @@ double Engine::ladder_build_sliced(const LadBatch& b, Tensor* L, int ns) {
 // Y_G[(ij), (ab) in batch] += alpha * X_G[(ij),(cd)] W_batch^T with the
 // batch rows already in slices (lad_ws_)
 void Engine::ladder_apply_sliced(const LadBatch& b, double alpha, Tensor* X,
-                                 Tensor* Y, int ns) {
+                                 Tensor* Y, int ns, const void* W) {
   const Layout& XL = X->lay;
   const int G = b.G;
   const int64_t M = XL.nrow[G], K = XL.ncol[G];
@@ -337,7 +339,7 @@ void Engine::ladder_apply_sliced(const LadBatch& b, double alpha, Tensor* X,
   TcProb t;
   std::memset(&t, 0, sizeof(t));
   t.a = slice_side(X, A, (int)M, (int)K, K, 0, ns, false, &cur);
-  t.b = {lad_ws_, nullptr, (int)b.rows, (int)Kp};
+  t.b = {W ? W : lad_ws_, nullptr, (int)b.rows, (int)Kp};
   t.C = C;
   t.M = (int)M;
   t.N = (int)b.rows;
@@ -448,6 +450,15 @@ void Engine::ladder_lin_apply(int which, double alpha, Tensor* X, Tensor* LW,
   ++Y->ver;
 }
 
+void Engine::ladder_keep_slices(int64_t bytes) {
+  lad_cache_cap_ = std::max<int64_t>(0, bytes);
+  if (bytes > 0) return;
+  if (lad_cache_.empty()) return;
+  for (auto& kv : lad_cache_) al.release(kv.second.data, kv.second.bytes);
+  lad_cache_.clear();
+  lad_cache_bytes_ = 0;
+}
+
 void Engine::ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
                         Tensor* Y) {
   if (stored) {
@@ -481,14 +492,54 @@ void Engine::ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
         e0 = get_event();
         cudaEventRecord(e0, st_);
       }
-      const double fb = ladder_build_sliced(b, L, ns);
+      // slices kept from an earlier application (same L version), or built
+      // now: into a kept buffer while the budget lasts, else the batch
+      // buffer
+      const void* W = nullptr;
+      double fb = 0;
+      if (lad_cache_cap_ > 0) {
+        std::ostringstream key;
+        key << b.G << ',' << b.ga << ',' << b.a0 << ',' << b.a1 << ',' << ns;
+        auto it = lad_cache_.find(key.str());
+        if (it != lad_cache_.end() && it->second.L == L &&
+            it->second.lver == L->ver) {
+          W = it->second.data;
+        } else {
+          int64_t ncol = 0;
+          for (int gc = 0; gc < dims_.h; ++gc)
+            ncol += (int64_t)dims_.n[SV][gc] * dims_.n[SV][gc ^ b.G];
+          const size_t bytes =
+              (size_t)ns * b.rows * slice_kp((int)ncol) * 2;
+          void* dst = nullptr;
+          if (it != lad_cache_.end() && it->second.bytes == bytes) {
+            dst = it->second.data;   // stale (new L): rebuilt in place
+          } else if (it == lad_cache_.end() &&
+                     lad_cache_bytes_ + (int64_t)bytes <= lad_cache_cap_ &&
+                     device_free_above(bytes, (size_t)8 << 30)) {
+            // (kept or rebuilt slices hold the same values, so the choice
+            // may depend on the free memory of the moment)
+            dst = al.alloc(bytes);
+            lad_cache_[key.str()] = {dst, bytes, 0, L};
+            lad_cache_bytes_ += (int64_t)bytes;
+            it = lad_cache_.find(key.str());
+          }
+          fb = ladder_build_sliced(b, L, ns, dst);
+          if (dst) {
+            it->second.lver = L->ver;
+            it->second.L = L;
+            W = dst;
+          }
+        }
+      } else {
+        fb = ladder_build_sliced(b, L, ns);
+      }
       if (prof_on_) {
         e1 = get_event();
         e2 = get_event();
         cudaEventRecord(e1, st_);
         cudaEventRecord(e2, st_);
       }
-      ladder_apply_sliced(b, alpha, T, R, ns);
+      ladder_apply_sliced(b, alpha, T, R, ns, W);
       if (prof_on_) {
         e3 = get_event();
         cudaEventRecord(e3, st_);

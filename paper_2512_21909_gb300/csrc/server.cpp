@@ -137,14 +137,15 @@ size_t packed_size(const std::vector<int>& n, const std::vector<int>& q,
 // ladder: stored integrals with their adjoint and slices (16 / 28 / 36
 // bytes per element for FP64 / MIXED / TC), or on the fly two batch
 // buffers, the batch slices and the adjoint batch slices of the density
-// sweep (measured peaks stay below five batches).
+// sweep (measured peaks stay below five batches) plus the batch slices
+// kept across applications (4 bytes per element, within their budget).
 struct Footprint {
   int64_t t2 = 0, w = 0, ovvv = 0, nnz = 0;
   size_t bytes = 0, ladder_bytes = 0;
 };
 
 Footprint footprint(const cdcc_job_desc& j, int precision, int ladder,
-                    double batch_gb, double perm_gb) {
+                    double batch_gb, double perm_gb, double slices_gb) {
   Footprint f;
   std::vector<int> o, v, q;
   if (!counts(j, o, v, q)) return f;
@@ -170,6 +171,10 @@ Footprint footprint(const cdcc_job_desc& j, int precision, int ladder,
     lad = 8.0 * (double)f.w * k;
   } else {
     lad = 5.5 * batch_gb * 1e9;
+    // BF16 batch slices kept across applications (two slices, float
+    // schedules only)
+    if (precision != CDCC_PREC_FP64 && slices_gb > 0)
+      lad += std::min(4.0 * (double)f.w, slices_gb * 1e9);
   }
   f.ladder_bytes = (size_t)lad;
   f.bytes = (size_t)(base + lad);
@@ -343,7 +348,9 @@ size_t cdcc_job_footprint(const cdcc_job_desc* job, int precision, int ladder,
   if (!job || !job->orb_irrep || !job->chol_irrep) return 0;
   cdcc_options d;
   cdcc_default_options(&d);
-  return footprint(*job, precision, ladder, batch_gb, d.perm_cache_gb).bytes;
+  return footprint(*job, precision, ladder, batch_gb, d.perm_cache_gb,
+                   d.ladder_slices_gb)
+      .bytes;
 }
 
 cdcc_status cdcc_server_create(cdcc_server** out, const cdcc_options* opt,
@@ -443,7 +450,7 @@ cdcc_status cdcc_submit(cdcc_server* s, const cdcc_job_desc* d,
   // ladder mode from the job's size only
   const Footprint fs =
       footprint(j->desc(), s->opt.precision, CDCC_LADDER_STORED, 0.0,
-                s->opt.perm_cache_gb);
+                s->opt.perm_cache_gb, s->opt.ladder_slices_gb);
   j->ladder = (double)fs.ladder_bytes <= s->sopt.stored_max_gb * 1e9
                   ? CDCC_LADDER_STORED
                   : CDCC_LADDER_OTF;
@@ -451,7 +458,7 @@ cdcc_status cdcc_submit(cdcc_server* s, const cdcc_job_desc* d,
     j->ladder = s->opt.ladder;
   const double bgb = s->opt.ladder_batch_gb > 0 ? s->opt.ladder_batch_gb : 2.0;
   j->est_bytes = footprint(j->desc(), s->opt.precision, j->ladder, bgb,
-                           s->opt.perm_cache_gb)
+                           s->opt.perm_cache_gb, s->opt.ladder_slices_gb)
                      .bytes;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stopping) return CDCC_ESTATE;

@@ -640,6 +640,14 @@ TcPlan tc_plan(const TcProb* p, int np, int s) {
   for (int i = 0; i < np; ++i)
     maxc = std::max(maxc, pl.swap ? p[i].M : p[i].N);
   pl.bn = maxc <= 32 ? 32 : maxc <= 64 ? 64 : maxc <= 128 ? 128 : 256;
+  // short K (a few K blocks per tile, as in the ladder builds with K = nL
+  // of one irrep): 128-wide column tiles with three stages in flight beat
+  // 256-wide ones with two (fused c3 build launch 462 -> 412 us; a 4048^3
+  // product with long K is 15 % slower with them, so only for short K)
+  int maxkb = 0;
+  for (int i = 0; i < np; ++i)
+    maxkb = std::max(maxkb, (p[i].K + TC_BK - 1) / TC_BK);
+  if (pl.bn == 256 && maxkb <= 8) pl.bn = 128;
   // at least two stages in flight: narrower column tiles otherwise
   while (pl.bn > 32 && TC_SMEM_BUDGET / (s * (TC_BM * 128 + pl.bn * 128)) < 2)
     pl.bn /= 2;
@@ -668,6 +676,32 @@ TcPlan tc_plan(const TcProb* p, int np, int s) {
   return pl;
 }
 
+}  // namespace
+
+namespace {
+// Largest dynamic shared memory of any launch: stages within the budget,
+// barriers, epilogue staging.  The attribute belongs to the kernel on the
+// device, shared by every host thread and stream, so it is set once to this
+// maximum: a per-launch value could be lowered by a concurrent launch of a
+// smaller configuration between another thread's set and launch.
+constexpr int TC_SMEM_MAX =
+    TC_SMEM_BUDGET + 1024 + 256 + TC_EPI_WARPS * TC_STG_BYTES;
+
+void tc_smem_attr(int smem) {
+  if (smem > TC_SMEM_MAX)
+    throw std::runtime_error("tc: shared memory plan above its maximum");
+  static std::once_flag once[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  std::call_once(once[dev], [] {
+    cudaFuncSetAttribute(tc_gemm_kernel<false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TC_SMEM_MAX);
+    cudaFuncSetAttribute(tc_gemm_kernel<true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TC_SMEM_MAX);
+  });
+}
 }  // namespace
 
 int64_t tc_sliced_scratch_doubles(const TcProb* p, int np, int nslice) {
@@ -731,10 +765,9 @@ int tc_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   L->scratch = scratch;
   L->err = d_err;
   const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
-  // stages, barriers, and four 32 x 17 double staging tiles for the output
+  // stages, barriers, and the epilogue warps' staging tiles
   const int smem = pl.stages * stage + 1024 + 256 + TC_EPI_WARPS * TC_STG_BYTES;
-  cudaFuncSetAttribute(tc_gemm_kernel<false>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  tc_smem_attr(smem);
   // persistent: one CTA per SM (at most one fits), tiles strided over them
   const int grid = std::max(1, std::min(tiles, sm_count()));
   tc_gemm_kernel<false><<<grid, TC_THREADS, smem, st>>>(*L);
@@ -794,8 +827,7 @@ int tc_gemm_ladder(const TcProb* p, int np, int nslice, const TcLadEpi* epi,
   L->lad_on = 1;
   const int stage = nslice * (TC_BM * 128 + pl.bn * 128);
   const int smem = pl.stages * stage + 1024 + 256 + TC_EPI_WARPS * TC_STG_BYTES;
-  cudaFuncSetAttribute(tc_gemm_kernel<true>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  tc_smem_attr(smem);
   const int grid = std::max(1, std::min(tiles, sm_count()));
   tc_gemm_kernel<true><<<grid, TC_THREADS, smem, st>>>(*L);
   delete L;

@@ -691,8 +691,21 @@ int oz_gemm_sliced(const TcProb* p, int np, double alpha, double beta,
   const int stage = nslice * (OZ_BM * 128 + OZ_BN * 128);
   // stages, barriers, and one 32 x 16 double staging tile per drain warp
   const int smem = OZ_STAGES * stage + 1024 + 256 + OZ_DRAIN_WARPS * 32 * 16 * 8;
-  cudaFuncSetAttribute(oz_gemm_kernel,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // the attribute is shared by every thread and stream: set once, to the
+  // largest launch (four slices), never lowered by a concurrent smaller one
+  constexpr int OZ_SMEM_MAX = OZ_STAGES * OZ_MAXS * (OZ_BM * 128 + OZ_BN * 128) +
+                              1024 + 256 + OZ_DRAIN_WARPS * 32 * 16 * 8;
+  if (smem > OZ_SMEM_MAX) throw std::runtime_error("oz: shared memory plan");
+  {
+    static std::once_flag once[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    std::call_once(once[dev], [] {
+      cudaFuncSetAttribute(oz_gemm_kernel,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           OZ_SMEM_MAX);
+    });
+  }
   // persistent: one CTA per SM (at most one fits), tiles strided over them
   const int grid = std::max(1, std::min(tiles, sm_count()));
   oz_gemm_kernel<<<grid, OZ_THREADS, smem, st>>>(*L);
