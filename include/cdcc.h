@@ -228,6 +228,45 @@ cdcc_status contract_df(cdcc_ctx *ctx, const double *metric, int nx,
                         const double *dB, const double *dM, double *g);
 
 /*
+ * Symmetry-adapted two-step Cholesky decomposition of the ERI matrix
+ * (Sec. 3.2, Algorithm 1; second step Eq. cv_2ndstep), context free.  The
+ * pair-integral matrix is block diagonal by the irrep of the basis pair;
+ * block G is given in factored form, (r|s) = sum_k B_G[r,k] B_G[s,k]
+ * (positive semidefinite), and its integrals are evaluated from B.
+ *   nirrep        1..8
+ *   npair[G]      pairs of irrep G; naux[G] columns of B_G
+ *   B             the blocks B_G (npair[G] x naux[G], row-major) back to
+ *                 back; host or device memory of `device`
+ *   tau           threshold: every residual |(r|s) - sum_P L_r L_s| ends
+ *                 below tau (> 0)
+ *   sigma         span factor of the qualified candidates (0 < sigma <= 1;
+ *                 the paper uses 1e-2); qmax: candidates per macro
+ *                 iteration (>= 1; the paper uses 1000)
+ *   device, stream  CUDA device and stream (0: the default stream)
+ *   ncv[G]        out (host): vectors (pivots) of irrep G
+ *   piv           out (host or device): the pivots' pair indices within
+ *                 their irrep, irrep blocks back to back, each in the
+ *                 order taken; piv_cap entries
+ *   L             out (host or device): the second-step vectors, for each
+ *                 irrep ncv[G] x npair[G] row-major, blocks back to back;
+ *                 L_cap doubles
+ *   stats         out (host, may be null): [macro iterations, micro
+ *                 iterations, first-step s, second-step s]
+ *   msg           out (may be null): message of a failed call (msg_len
+ *                 bytes, NUL terminated)
+ * FP64 throughout.  Errors: CDCC_EINVAL (sizes, thresholds), CDCC_ENOMEM
+ * (device memory, or piv_cap / L_cap too small: ncv is filled, retry with
+ * the sizes it gives), CDCC_ENUMERIC (a non-finite diagonal, or the
+ * pivots' metric not positive definite), CDCC_ECUDA.
+ */
+cdcc_status cdcc_cd_two_step(int nirrep, const int32_t *npair,
+                             const int32_t *naux, const double *B,
+                             double tau, double sigma, int qmax, int device,
+                             void *stream, int32_t *ncv, int32_t *piv,
+                             int64_t piv_cap, double *L, int64_t L_cap,
+                             double *stats, char *msg, int msg_len);
+
+/*
  * Error report of a result (the precision schedule of Sec. 2 / cdcc_options):
  * what the schedule's reduced-precision arithmetic changed, measured against
  * FP64 DFMA arithmetic at the same converged amplitudes t and multipliers

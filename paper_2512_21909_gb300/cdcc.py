@@ -295,6 +295,61 @@ def contract_df(ctx, metric, dB, dM):
     return g[:nx]
 
 
+def cd_two_step(npair, naux, B, tau, sigma=1e-2, qmax=1000, device=0,
+                max_vectors=None):
+    """Symmetry-adapted two-step Cholesky decomposition (see
+    include/cdcc.h, cdcc_cd_two_step): npair, naux per irrep; B the packed
+    factor blocks (host or device array).  Returns (pivots, vectors, stats):
+    pivots[G] (pair indices in the order taken), vectors[G]
+    (ncv x npair numpy arrays), stats [macro, micro, first s, second s]."""
+    lib = load()
+    lib.cdcc_cd_two_step.argtypes = (
+        [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+         ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+         ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_char_p,
+         ctypes.c_int])
+    lib.cdcc_cd_two_step.restype = ctypes.c_int
+    h = len(npair)
+    npa = np.ascontiguousarray(npair, dtype=np.int32)
+    nax = np.ascontiguousarray(naux, dtype=np.int32)
+    Bp, Bk = _ptr(_f64(B))
+    ncv = np.zeros(h, np.int32)
+    stats = np.zeros(4)
+    msg = ctypes.create_string_buffer(256)
+    # outputs sized for the factor's rank (plus a margin); if that is too
+    # small the call reports the counts and is repeated with exact sizes
+    per = [min(int(n), int(k) + 64) for n, k in zip(npair, naux)]
+    if max_vectors is not None:
+        per = [min(int(n), int(max_vectors)) for n in npair]
+    for _ in range(2):
+        piv = np.zeros(max(sum(per), 1), np.int32)
+        L = np.zeros(max(sum(c * int(n) for c, n in zip(per, npair)), 1))
+        st = lib.cdcc_cd_two_step(
+            h, npa.ctypes.data_as(ctypes.c_void_p),
+            nax.ctypes.data_as(ctypes.c_void_p), Bp, float(tau),
+            float(sigma), int(qmax), int(device), None,
+            ncv.ctypes.data_as(ctypes.c_void_p),
+            piv.ctypes.data_as(ctypes.c_void_p), int(piv.size),
+            L.ctypes.data_as(ctypes.c_void_p), int(L.size),
+            stats.ctypes.data_as(ctypes.c_void_p), msg, 256)
+        if st == CDCC_ENOMEM and int(ncv.sum()) > 0 and \
+                any(int(c) > p for c, p in zip(ncv, per)):
+            per = [int(c) for c in ncv]
+            continue
+        break
+    if st != CDCC_OK:
+        raise CdccError(st, msg.value.decode(errors="replace"))
+    pivots, vectors, po, lo = [], [], 0, 0
+    for g in range(h):
+        k, n = int(ncv[g]), int(npair[g])
+        pivots.append(piv[po:po + k].tolist())
+        vectors.append(L[lo:lo + k * n].reshape(k, n).copy())
+        po += k
+        lo += k * n
+    return pivots, vectors, stats
+
+
 def cdcc_error_estimate(ctx, dL=None, nx=None, x_irrep=None):
     """(dE, dg[nx]): change of E and g caused by the schedule's reduced
     precision, measured against FP64 at the converged t and lambda."""

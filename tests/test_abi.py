@@ -42,7 +42,7 @@ def test_all_declared_symbols_exported(lib):
     for n in ("cdcc_server_create", "cdcc_submit", "cdcc_poll", "cdcc_wait",
               "cdcc_server_destroy", "cdcc_job_footprint",
               "cdcc_energy_error", "contract_df", "cdcc_metric_size",
-              "cdcc_contract_dL_noalloc"):
+              "cdcc_contract_dL_noalloc", "cdcc_cd_two_step"):
         assert n in names, n
     for n in names:
         assert hasattr(lib, n), n
@@ -101,3 +101,19 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         cdcc.load()
     with pytest.raises(RuntimeError):
         cdcc.cdcc_default_options()
+
+
+@pytest.mark.parametrize("kw", [dict(tau=0.0), dict(tau=float("nan")),
+                                dict(sigma=0.0), dict(sigma=1.5),
+                                dict(qmax=0), dict(nirrep=9),
+                                dict(npair=-1)])
+def test_two_step_cd_rejects_bad_arguments(lib, kw):
+    # checked before any device call: no GPU needed
+    nirrep = kw.get("nirrep", 1)
+    npair = [kw.get("npair", 3)] * nirrep
+    naux = [2] * nirrep
+    B = np.ones(max(sum(max(n, 0) * k for n, k in zip(npair, naux)), 1))
+    with pytest.raises(cdcc.CdccError) as e:
+        cdcc.cd_two_step(npair, naux, B, kw.get("tau", 1e-6),
+                         sigma=kw.get("sigma", 1e-2), qmax=kw.get("qmax", 10))
+    assert e.value.status == cdcc.CDCC_EINVAL
