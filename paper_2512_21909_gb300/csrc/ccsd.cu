@@ -231,8 +231,12 @@ void prepare(cdcc_ctx* c) {
 // one engine primitive so that the same code, recorded, yields the adjoints.
 void residual(cdcc_ctx* c) {
   Engine& e = *c->eng;
+  // intermediates: written only by the engine operations below, so their
+  // permuted copies can be reused while they do not change
   auto T = [&](const char* n, std::vector<int> sp, int split) {
-    return e.tensor(n, sp, split);
+    Tensor* t = e.tensor(n, sp, split);
+    t->cacheable = true;
+    return t;
   };
   Tensor *T1 = c->T1, *T2 = c->T2;
   Tensor *Loo = c->Loo, *Lov = c->Lov, *Lvo = c->Lvo, *Lvv = c->Lvv;
@@ -336,20 +340,22 @@ void residual(cdcc_ctx* c) {
   e.contract(1.0, t2s, "ijcd", Govov, "kcld", 1.0, Wh, "kilj");
   e.contract(1.0, t2s, "klab", Wh, "kilj", 1.0, Rr, "ijab");     // hole-hole
   // rings: spin-integrated P(ij)P(ab) t_im^ae W_mbej, direct (WA) and
-  // exchange (WC) spin patterns
-  Tensor* WA = T("WA", {SO, SV, SV, SO}, 2);
-  e.axpy(1.0, Govvo, "mebj", 0.0, WA, "mbej");
-  e.contract(0.5, u, "jnbf", Govov, "menf", 1.0, WA, "mbej");
-  e.contract(-0.5, t2s, "jnbf", Govov, "mfne", 1.0, WA, "mbej");
-  Tensor* WC = T("WC", {SO, SV, SV, SO}, 2);
-  e.axpy(-1.0, Goovv, "mjbe", 0.0, WC, "mbej");
-  e.contract(0.5, t2s, "jnfb", Govov, "mfne", 1.0, WC, "mbej");
-  Tensor* Rg = T("Ring", {SO, SO, SV, SV}, 2);
-  e.contract(1.0, WA, "mbej", u, "imae", 0.0, Rg, "ijab");
-  e.contract(1.0, WC, "mbej", t2s, "imae", 1.0, Rg, "ijab");
-  e.contract(1.0, WC, "mbei", t2s, "mjae", 1.0, Rg, "ijab");
-  e.axpy(1.0, Rg, "ijab", 1.0, Rr, "ijab");
-  e.axpy(1.0, Rg, "jiba", 1.0, Rr, "ijab");
+  // exchange (WC) spin patterns.  W_mbej is stored with rows (m,e) and
+  // columns (j,b), and the ring sum Rg_ij^ab with rows (j,b) and columns
+  // (i,a): the layouts in which the products below write and read them.
+  Tensor* WA = T("WA", {SO, SV, SO, SV}, 2);
+  e.axpy(1.0, Govvo, "mebj", 0.0, WA, "mejb");
+  e.contract(0.5, u, "jnbf", Govov, "menf", 1.0, WA, "mejb");
+  e.contract(-0.5, t2s, "jnbf", Govov, "mfne", 1.0, WA, "mejb");
+  Tensor* WC = T("WC", {SO, SV, SO, SV}, 2);
+  e.axpy(-1.0, Goovv, "mjbe", 0.0, WC, "mejb");
+  e.contract(0.5, t2s, "jnfb", Govov, "mfne", 1.0, WC, "mejb");
+  Tensor* Rg = T("Ring", {SO, SV, SO, SV}, 2);
+  e.contract(1.0, WA, "mejb", u, "imae", 0.0, Rg, "jbia");
+  e.contract(1.0, WC, "mejb", t2s, "imae", 1.0, Rg, "jbia");
+  e.contract(1.0, WC, "meib", t2s, "mjae", 1.0, Rg, "jbia");
+  e.axpy(1.0, Rg, "jbia", 1.0, Rr, "ijab");
+  e.axpy(1.0, Rg, "iajb", 1.0, Rr, "ijab");
   // Fock-like terms
   Tensor* Fvv2 = T("Fvv2", {SV, SV}, 1);
   e.axpy(1.0, Fvv, "bc", 0.0, Fvv2, "bc");

@@ -228,13 +228,32 @@ Tensor* Engine::permuted_constant(Tensor* T, const std::string& tl,
   if (!device_free_above((size_t)bytes, (size_t)8 << 30)) return nullptr;
   Tensor* P = new_tensor("perm:" + key, sp, (int)r.size(), T->lay.gtot);
   P->constant = true;
-  P->frozen = T->frozen;   // its slices count against the frozen budget
+  // slices of a copy of a frozen or changing tensor count against the
+  // bounded budget (and the free-memory guard)
+  P->frozen = T->frozen || !T->constant;
   P->ladder = T->ladder;
   axpy_raw(1.0, T->lay, T->d, tl, 0.0, P->lay, P->d, rc);
   P->ver = 1;
   perm_const_[key] = {P, T->ver, T};
   perm_const_bytes_ += bytes;
   return P;
+}
+
+// The kept copy of T in layout (r, c) exists and is of T's current version.
+bool Engine::permuted_current(Tensor* T, const std::string& tl,
+                              const std::string& r, const std::string& c) {
+  const std::string rc = r + c;
+  if ((int)rc.size() != T->lay.rank || (int)tl.size() != T->lay.rank)
+    return false;
+  std::string key = T->name + '|';
+  for (char x : rc) {
+    const size_t p = tl.find(x);
+    if (p == std::string::npos) return false;
+    key += (char)('0' + (int)p);
+  }
+  key += ':' + std::to_string(r.size());
+  auto it = perm_const_.find(key);
+  return it != perm_const_.end() && it->second.src_ver == T->ver;
 }
 
 int Engine::sig_of(const std::string& s) {
@@ -605,9 +624,11 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
 
   // a constant operand whose permuted copy is (or can be) kept costs
   // nothing per call
+  // ... and so does a changing one whose copy of this version exists
   auto perm_cost = [&](Tensor* T, const std::string& tl, const std::string& r,
                        const std::string& c) -> int64_t {
     if (T->constant && permuted_constant(T, tl, r, c, false)) return 0;
+    if (T->cacheable && permuted_current(T, tl, r, c)) return 0;
     return T->lay.size;
   };
   auto matches = [](const Tensor* T, const std::string& tl,
@@ -661,7 +682,7 @@ void Engine::contract(double alpha, Tensor* A, const char* ia_, Tensor* B,
                  const std::string& c) -> Mat {
     bool tr;
     if (matches(T, tl, r, c, tr)) return {T->d, &T->lay, tr, T};
-    if (T->constant) {
+    if (T->constant || T->cacheable) {
       Tensor* Pc = permuted_constant(T, tl, r, c, true);
       if (Pc) return {Pc->d, &Pc->lay, false, Pc};
     }

@@ -61,6 +61,9 @@ struct Tensor {
   bool ladder = false;
   // constant only while the adjoint sweeps run (Engine::freeze_tape_operands)
   bool frozen = false;
+  // written only through engine operations (each bumps ver), so a permuted
+  // copy may be kept and reused while ver is unchanged
+  bool cacheable = false;
   uint64_t ver = 0;   // bumped on every write
 };
 
@@ -382,6 +385,8 @@ class Engine {
   Tensor* permuted_constant(Tensor* T, const std::string& tl,
                             const std::string& r, const std::string& c,
                             bool create);
+  bool permuted_current(Tensor* T, const std::string& tl,
+                        const std::string& r, const std::string& c);
   // sets the signature for the launches issued in its scope (profiling on)
   struct SigScope {
     Engine* e;
