@@ -133,6 +133,11 @@ typedef struct {
                                kept while 8 GB stay free, freed before the
                                density sweep); 0 = rebuild every
                                application (default 48)                     */
+    int ladder_pm;          /* ladder on the fly with symmetric /
+                               antisymmetric (+/-) packing of the pairs ij,
+                               ab and cd (Sec. 2.3): two products over the
+                               canonical pairs, a quarter of the flops of
+                               the plain map (default 1; 0 = plain map)     */
 } cdcc_options;
 
 typedef struct cdcc_ctx cdcc_ctx;

@@ -43,7 +43,8 @@ class cdcc_options(ctypes.Structure):
                 ("fock_model", ctypes.c_int),
                 ("ladder_linearize", ctypes.c_int),
                 ("perm_cache_gb", ctypes.c_double),
-                ("ladder_slices_gb", ctypes.c_double)]
+                ("ladder_slices_gb", ctypes.c_double),
+                ("ladder_pm", ctypes.c_int)]
 
 
 class CdccError(RuntimeError):

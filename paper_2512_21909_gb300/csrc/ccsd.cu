@@ -1337,6 +1337,7 @@ void init_ctx(cdcc_ctx* c, int nirrep, int nocc, int nvir, int nchol,
     const double gb = c->opt.ladder_batch_gb > 0 ? c->opt.ladder_batch_gb
                                                  : 2.0;
     e.ladder_batch_bytes = (int64_t)(gb * 1e9);
+    e.set_ladder_pm(c->opt.ladder_pm != 0);
   }
   {
     std::vector<double> h = to_host(c, c->hoo);
@@ -1453,6 +1454,7 @@ void cdcc_default_options(cdcc_options* o) {
   o->ladder_linearize = 1;
   o->perm_cache_gb = 32.0;
   o->ladder_slices_gb = 48.0;
+  o->ladder_pm = 1;
 }
 
 cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,

@@ -69,6 +69,10 @@ Engine::~Engine() {
   if (lad_x_) al.release(lad_x_, (size_t)lad_n_ * 8);
   if (lad_w_) al.release(lad_w_, (size_t)lad_n_ * 8);
   if (lad_ws_) al.release(lad_ws_, lad_ws_bytes_);
+  if (pm_.d_tab) al.release(pm_.d_tab, pm_.bytes);
+  if (pm_a_) al.release(pm_a_, (size_t)pm_a_n_ * 8);
+  if (pm_w_) al.release(pm_w_, (size_t)pm_w_n_ * 8);
+  if (pm_as_) al.release(pm_as_, pm_as_bytes_);
   for (auto& kv : lad_cache_) al.release(kv.second.data, kv.second.bytes);
   for (auto& kv : slice_cache_) {
     al.release(kv.second.data, kv.second.bytes);

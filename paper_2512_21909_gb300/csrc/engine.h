@@ -198,6 +198,12 @@ class Engine {
   // keep up to `bytes` of on-the-fly ladder batch slices across ladder
   // applications (0 frees them and stops keeping)
   void ladder_keep_slices(int64_t bytes);
+  // on-the-fly ladder with symmetric/antisymmetric (+/-) packing of the
+  // three index pairs (Sec. 2.3): a quarter of the product flops, for
+  // pair-symmetric amplitudes (it returns the ladder of the pair-symmetrised
+  // input)
+  void set_ladder_pm(bool on) { ladder_pm_ = on; }
+  bool ladder_pm() const { return ladder_pm_; }
   // a rejected launch (bad configuration, resources) is an error, never a
   // silently missing result
   static void check_launch() {
@@ -327,6 +333,30 @@ class Engine {
   LadderLin lin_[2];
   void ladder_lin_apply(int which, double alpha, Tensor* X, Tensor* LW,
                         bool stored, Tensor* Y);
+  // +/- packed ladder: index tables per layout (device, one allocation)
+  struct PmBatch {
+    LadBatch b;
+    int nv;          // canonical (a,b) rows of the batch
+    int64_t vrow;    // offset of its [3][nv] table in d_tab
+  };
+  struct PmPlan {
+    std::string key;
+    int uo[MAXIRR] = {}, uv[MAXIRR] = {};
+    int64_t orow[MAXIRR] = {}, vcol[MAXIRR] = {};   // offsets in d_tab
+    std::vector<PmBatch> batches;
+    int* d_tab = nullptr;
+    size_t bytes = 0;
+    int64_t max_a = 0, max_w = 0;   // doubles of A+- and of a batch's W+-
+  };
+  PmPlan pm_;
+  bool ladder_pm_ = false;
+  double* pm_a_ = nullptr;   // A+ | A- of one pair irrep (FP64)
+  double* pm_w_ = nullptr;   // W+ | W- of one batch (FP64)
+  int64_t pm_a_n_ = 0, pm_w_n_ = 0;
+  void* pm_as_ = nullptr;    // BF16 slices of A+ | A-
+  size_t pm_as_bytes_ = 0;
+  const PmPlan& pm_plan(const Layout& TL);
+  void ladder_map_pm(double alpha, Tensor* X, Tensor* L, Tensor* Y);
   int tc_override_ = -1;
   double* lad_x_ = nullptr;
   double* lad_w_ = nullptr;

@@ -173,4 +173,25 @@ struct LadPerm {
 int ladder_permute(const LadPerm& P, bool inverse, const double* src,
                    double* dst, int rows, cudaStream_t st);
 
+// +/- packed ladder (ladder_pm.cu; Sec. 2.3).  Inside one DPD block of
+// pair irrep G (row length ncol): orow[2][uo] the row offsets of (i,j) and
+// (j,i) per canonical occupied pair, vcol[2][uv] the column offsets of
+// (c,d) and (d,c) per canonical virtual pair, vrow[3][nv] per canonical
+// (a,b) of a row batch its row in the batch's (ab|cd) rows W and the
+// columns of (a,b) and (b,a) in Y (-1: a == b).
+//   pm_pack_x: Ap/Am[r][u] = (X11 + X22 +- (X12 + X21)) / 4 of rows r1, r2
+//              and columns c1, c2 (uo x uv, row-major)
+//   pm_pack_w: Wp/Wm[v][u] = W[row][c1] +- W[row][c2] (c1 == c2: W, 0)
+//   pm_unpack: Y[(ij),(ab)] += alpha (Sp + Sm) and the swapped elements
+//              with the signs of the pair swaps (Sp, Sm: uo x nv)
+int pm_pack_x(const double* X, int64_t ncol, const int* orow, int uo,
+              const int* vcol, int uv, double* Ap, double* Am,
+              cudaStream_t st);
+int pm_pack_w(const double* W, int64_t ncol, const int* vrow, int nv,
+              const int* vcol, int uv, double* Wp, double* Wm,
+              cudaStream_t st);
+int pm_unpack(const double* Sp, const double* Sm, int uo, int nv,
+              const int* orow, const int* vrow, double alpha, double* Y,
+              int64_t ncol, cudaStream_t st);
+
 }  // namespace cdcc

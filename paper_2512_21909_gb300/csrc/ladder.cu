@@ -465,6 +465,10 @@ void Engine::ladder_map(double alpha, Tensor* X, Tensor* LW, bool stored,
     contract(alpha, X, "ijcd", LW, "abcd", 1.0, Y, "ijab");
     return;
   }
+  if (ladder_pm_) {
+    ladder_map_pm(alpha, X, LW, Y);
+    return;
+  }
   Tensor* T = X;
   Tensor* L = LW;
   Tensor* R = Y;
@@ -683,6 +687,287 @@ void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
     cudaEvent_t tr_b = get_event();
     cudaEventRecord(tr_b, st_);
     trace_pending_.push_back({"ladder on the fly, adjoint", tr_a, tr_b, fl});
+  }
+  release_scratch();
+}
+
+
+// ---------------------------------------------------------------------------
+// +/- packed on-the-fly ladder (Sec. 2.3; arithmetic in ladder_pm.cu).
+// Canonical pairs (p,q) of an index pair: irrep(p) > irrep(q), or the same
+// irrep and p >= q.  For the pair irrep G the canonical (a,b) rows are the
+// row batches with ga > gb (all rows) and, for G = 0 (ga == gb), the rows
+// with b <= a of each batch; batches with ga < gb are not built at all.
+// Per batch: the (ab|cd) rows W as in the plain map, then
+//   W+- = W[.,(cd)] +- W[.,(dc)]   (pm_pack_w)
+//   S+- = A+- W+-^T                 (two GEMMs: canonical ij x ab x cd)
+//   Y  += the signed combinations of S+ and S- (pm_unpack)
+// with A+- packed once per pair irrep from X (pm_pack_x).  With float
+// slices the BF16 slices of W+- are kept across applications (they depend
+// on L only), within the budget of ladder_keep_slices.
+
+const Engine::PmPlan& Engine::pm_plan(const Layout& TL) {
+  std::ostringstream ks;
+  ks << TL.key() << '/' << ladder_batch_bytes;
+  if (pm_.d_tab && pm_.key == ks.str()) return pm_;
+  if (pm_.d_tab) al.release(pm_.d_tab, pm_.bytes);
+  pm_ = PmPlan();
+  const int h = dims_.h;
+  std::vector<int> tab;
+  auto off32 = [](int64_t v) {
+    if (v < 0 || v > INT32_MAX)
+      throw EngineError("ladder +/-: block offset beyond 32 bits");
+    return (int)v;
+  };
+  for (int G = 0; G < h; ++G) {
+    if (TL.nrow[G] == 0 || TL.ncol[G] == 0) continue;
+    // canonical occupied pairs: rows (i,j) and (j,i)
+    std::vector<int> r1, r2;
+    for (int gi = 0; gi < h; ++gi) {
+      const int gj = gi ^ G;
+      if (gi < gj) continue;
+      const int ni = dims_.n[SO][gi], nj = dims_.n[SO][gj];
+      const int64_t o1 = TL.rsub[G * TL.ncode_r + gi];
+      const int64_t o2 = TL.rsub[G * TL.ncode_r + gj];
+      for (int i = 0; i < ni; ++i)
+        for (int j = 0; j < (gi == gj ? i + 1 : nj); ++j) {
+          r1.push_back(off32(o1 + (int64_t)i * nj + j));
+          r2.push_back(off32(o2 + (int64_t)j * ni + i));
+        }
+    }
+    // canonical virtual pairs: columns (c,d) and (d,c)
+    std::vector<int> c1, c2;
+    for (int gc = 0; gc < h; ++gc) {
+      const int gd = gc ^ G;
+      if (gc < gd) continue;
+      const int nc = dims_.n[SV][gc], nd = dims_.n[SV][gd];
+      const int64_t o1 = TL.csub[G * TL.ncode_c + gc];
+      const int64_t o2 = TL.csub[G * TL.ncode_c + gd];
+      for (int c = 0; c < nc; ++c)
+        for (int d = 0; d < (gc == gd ? c + 1 : nd); ++d) {
+          c1.push_back(off32(o1 + (int64_t)c * nd + d));
+          c2.push_back(off32(o2 + (int64_t)d * nc + c));
+        }
+    }
+    pm_.uo[G] = (int)r1.size();
+    pm_.uv[G] = (int)c1.size();
+    pm_.orow[G] = (int64_t)tab.size();
+    tab.insert(tab.end(), r1.begin(), r1.end());
+    tab.insert(tab.end(), r2.begin(), r2.end());
+    pm_.vcol[G] = (int64_t)tab.size();
+    tab.insert(tab.end(), c1.begin(), c1.end());
+    tab.insert(tab.end(), c2.begin(), c2.end());
+    pm_.max_a = std::max<int64_t>(pm_.max_a,
+                                  2 * (int64_t)r1.size() * (int64_t)c1.size());
+  }
+  for (const LadBatch& b : ladder_batches(TL)) {
+    const int G = b.G, ga = b.ga, gb = ga ^ G;
+    if (ga < gb || pm_.uo[G] == 0 || pm_.uv[G] == 0) continue;
+    const int na = dims_.n[SV][ga], nb = dims_.n[SV][gb];
+    const int64_t oab = TL.csub[G * TL.ncode_c + ga];
+    const int64_t oba = TL.csub[G * TL.ncode_c + gb];
+    std::vector<int> lr, y1, y2;
+    for (int a = b.a0; a < b.a1; ++a)
+      for (int bb = 0; bb < (ga == gb ? a + 1 : nb); ++bb) {
+        lr.push_back(off32((int64_t)(a - b.a0) * nb + bb));
+        y1.push_back(off32(oab + (int64_t)a * nb + bb));
+        y2.push_back(ga == gb && a == bb
+                         ? -1
+                         : off32(oba + (int64_t)bb * na + a));
+      }
+    if (lr.empty()) continue;
+    PmBatch pb;
+    pb.b = b;
+    pb.nv = (int)lr.size();
+    pb.vrow = (int64_t)tab.size();
+    tab.insert(tab.end(), lr.begin(), lr.end());
+    tab.insert(tab.end(), y1.begin(), y1.end());
+    tab.insert(tab.end(), y2.begin(), y2.end());
+    pm_.batches.push_back(pb);
+    pm_.max_w = std::max(pm_.max_w, 2 * (int64_t)pb.nv * pm_.uv[G]);
+  }
+  if (!tab.empty()) {
+    pm_.bytes = tab.size() * sizeof(int);
+    pm_.d_tab = (int*)al.alloc(pm_.bytes);
+    // pageable source: the copy is complete (staged) when the call returns
+    LCK(cudaMemcpyAsync(pm_.d_tab, tab.data(), pm_.bytes,
+                        cudaMemcpyHostToDevice, st_));
+  }
+  pm_.key = ks.str();
+  return pm_;
+}
+
+void Engine::ladder_map_pm(double alpha, Tensor* T, Tensor* L, Tensor* R) {
+  ++R->ver;
+  SigScope sig(this, "ladder on the fly");
+  cudaEvent_t tr_a = nullptr;
+  if (prof_on_) {
+    tr_a = get_event();
+    cudaEventRecord(tr_a, st_);
+  }
+  const PmPlan& P = pm_plan(T->lay);
+  int64_t need = 0;
+  for (const PmBatch& pb : P.batches)
+    need = std::max(need, pb.b.rows * T->lay.ncol[pb.b.G]);
+  ladder_reserve(need);
+  if (P.max_a > pm_a_n_) {
+    if (pm_a_) al.release(pm_a_, (size_t)pm_a_n_ * 8);
+    pm_a_ = nullptr;
+    pm_a_n_ = 0;
+    pm_a_ = (double*)al.alloc((size_t)P.max_a * 8);
+    pm_a_n_ = P.max_a;
+  }
+  if (P.max_w > pm_w_n_) {
+    if (pm_w_) al.release(pm_w_, (size_t)pm_w_n_ * 8);
+    pm_w_ = nullptr;
+    pm_w_n_ = 0;
+    pm_w_ = (double*)al.alloc((size_t)P.max_w * 8);
+    pm_w_n_ = P.max_w;
+  }
+  const int prec = active_precision();
+  const bool split = prec >= 1 && prec <= 3 && d_err != nullptr;
+  const int ns = prec;
+  double fl = 0;
+  int curG = -1;
+  bool a_sliced = false;
+  for (const PmBatch& pb : P.batches) {
+    const LadBatch& b = pb.b;
+    const int G = b.G;
+    const int uo = P.uo[G], uv = P.uv[G], nv = pb.nv;
+    const int64_t ncol = T->lay.ncol[G];
+    if (ncol != R->lay.ncol[G] || T->lay.nrow[G] != R->lay.nrow[G])
+      throw EngineError("internal: ladder +/- layouts differ");
+    const int* orow = P.d_tab + P.orow[G];
+    const int* vcol = P.d_tab + P.vcol[G];
+    const int* vrow = P.d_tab + pb.vrow;
+    double* Ap = pm_a_;
+    double* Am = pm_a_ + (int64_t)uo * uv;
+    if (G != curG) {
+      curG = G;
+      a_sliced = false;
+      const double* X = T->d + T->lay.blk_off[G];
+      timed(K_PERM, 48.0 * uo * (double)uv, [&] {
+        return pm_pack_x(X, ncol, orow, uo, vcol, uv, Ap, Am, st_);
+      });
+    }
+    const int64_t Kp = slice_kp(uv);
+    // kept BF16 slices of W+ | W- (float slices), or a buffer for them
+    const bool tcs = split && tc_shape(uo, nv, uv);
+    const void* Ws = nullptr;
+    void* dst = nullptr;
+    if (tcs && lad_cache_cap_ > 0) {
+      std::ostringstream key;
+      key << "pm," << G << ',' << b.ga << ',' << b.a0 << ',' << b.a1 << ','
+          << ns;
+      const size_t bytes = (size_t)2 * ns * nv * Kp * 2;
+      auto it = lad_cache_.find(key.str());
+      if (it != lad_cache_.end() && it->second.L == L &&
+          it->second.lver == L->ver && it->second.bytes == bytes) {
+        Ws = it->second.data;
+      } else if (it != lad_cache_.end() && it->second.bytes == bytes) {
+        dst = it->second.data;   // stale (new L): rebuilt in place
+        it->second.lver = L->ver;
+        it->second.L = L;
+      } else if (it == lad_cache_.end() &&
+                 lad_cache_bytes_ + (int64_t)bytes <= lad_cache_cap_ &&
+                 device_free_above(bytes, (size_t)8 << 30)) {
+        dst = al.alloc(bytes);
+        lad_cache_[key.str()] = {dst, bytes, L->ver, L};
+        lad_cache_bytes_ += (int64_t)bytes;
+      }
+    }
+    double* Wp = pm_w_;
+    double* Wm = pm_w_ + (int64_t)nv * uv;
+    if (!Ws) {
+      fl += ladder_build(b, L);   // (ab|cd) rows of the batch -> lad_w_
+      timed(K_PERM, 32.0 * nv * (double)uv, [&] {
+        return pm_pack_w(lad_w_, ncol, vrow, nv, vcol, uv, Wp, Wm, st_);
+      });
+      if (dst) {
+        uint8_t* d8 = (uint8_t*)dst;
+        timed(K_OTHER, 32.0 * nv * (double)uv, [&] {
+          return split_float(Wp, nv, uv, uv, 0, ns, d8, st_) +
+                 split_float(Wm, nv, uv, uv, 0, ns,
+                             d8 + (size_t)ns * nv * Kp * 2, st_);
+        });
+        Ws = dst;
+      }
+    }
+    double* S = scratch(2 * (int64_t)uo * nv);
+    double* Sp = S;
+    double* Sm = S + (int64_t)uo * nv;
+    const double fa = 4.0 * uo * (double)nv * uv;
+    if (Ws) {
+      // both products on pre-sliced operands, one grouped launch
+      const size_t abytes = (size_t)2 * ns * uo * Kp * 2;
+      if (!a_sliced) {
+        if (abytes > pm_as_bytes_) {
+          if (pm_as_) al.release(pm_as_, pm_as_bytes_);
+          pm_as_ = nullptr;
+          pm_as_bytes_ = 0;
+          pm_as_ = al.alloc(abytes);
+          pm_as_bytes_ = abytes;
+        }
+        uint8_t* a8 = (uint8_t*)pm_as_;
+        timed(K_OTHER, 32.0 * uo * (double)uv, [&] {
+          return split_float(Ap, uo, uv, uv, 0, ns, a8, st_) +
+                 split_float(Am, uo, uv, uv, 0, ns,
+                             a8 + (size_t)ns * uo * Kp * 2, st_);
+        });
+        a_sliced = true;
+      }
+      TcProb t[2];
+      std::memset(t, 0, sizeof(t));
+      for (int q = 0; q < 2; ++q) {
+        t[q].a = {(const uint8_t*)pm_as_ + (size_t)q * ns * uo * Kp * 2,
+                  nullptr, uo, (int)Kp};
+        t[q].b = {(const uint8_t*)Ws + (size_t)q * ns * nv * Kp * 2, nullptr,
+                  nv, (int)Kp};
+        t[q].C = q == 0 ? Sp : Sm;
+        t[q].M = uo;
+        t[q].N = nv;
+        t[q].K = uv;
+        t[q].ldc = nv;
+      }
+      tc_flops += (int64_t)fa;
+      const int64_t sk = tc_sliced_scratch_doubles(t, 2, ns);
+      double* skb = sk > 0 ? scratch(sk) : nullptr;
+      timed(K_TC, fa, [&] {
+        return tc_gemm_sliced(t, 2, 1.0, 0.0, ns, skb, d_err, st_);
+      });
+    } else {
+      GemmProb g[2];
+      std::memset(g, 0, sizeof(g));
+      for (int q = 0; q < 2; ++q) {
+        g[q].A = q == 0 ? Ap : Am;
+        g[q].lda = uv;
+        g[q].B = q == 0 ? Wp : Wm;
+        g[q].tb = 1;
+        g[q].ldb = uv;
+        g[q].C = q == 0 ? Sp : Sm;
+        g[q].ldc = nv;
+        g[q].M = uo;
+        g[q].N = nv;
+        g[q].K = uv;
+      }
+      const Mat ma{pm_a_, nullptr, false, nullptr};
+      const Mat mw{pm_w_, nullptr, false, nullptr};
+      run_gemms(g, 2, ma, mw, 1.0, 0.0);
+    }
+    fl += fa;
+    double* Y = R->d + R->lay.blk_off[G];
+    timed(K_PERM, 80.0 * uo * (double)nv, [&] {
+      return pm_unpack(Sp, Sm, uo, nv, orow, vrow, alpha, Y, ncol, st_);
+    });
+    release_scratch();   // stream order: the next batch may reuse it
+  }
+  if (tr_a) {
+    cudaEvent_t tr_b = get_event();
+    cudaEventRecord(tr_b, st_);
+    trace_pending_.push_back(
+        {std::string("ladder on the fly (ijcd,Pac,Pbd->ijab) [") +
+             (prec >= 12 ? "exact" : prec > 0 ? "split" : "fp64") + ", +/-]",
+         tr_a, tr_b, fl});
   }
   release_scratch();
 }

@@ -67,13 +67,16 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("pm", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("batch_gb", [1e-9, 2.5e-6, 2.0])
-def test_on_the_fly_ladder_matches_oracle(cd, name, batch_gb):
+def test_on_the_fly_ladder_matches_oracle(cd, name, batch_gb, pm):
+    # pm = 1: the +/- packed map (canonical pairs, two products)
     s = CASES[name]()
     dL = make_displacements(s, 3)
     r = oracle_run(s)
-    gg = run(cd, s, dL, ladder=cd.LADDER_OTF, ladder_batch_gb=batch_gb)
+    gg = run(cd, s, dL, ladder=cd.LADDER_OTF, ladder_batch_gb=batch_gb,
+             ladder_pm=pm)
     assert gg["mode"] == cd.LADDER_OTF
     G_or = pack_dense(s, r["G"].numpy())
     assert abs(gg["e"] - r["cc"]["E_corr"]) < 1e-10
@@ -82,12 +85,14 @@ def test_on_the_fly_ladder_matches_oracle(cd, name, batch_gb):
     assert np.abs(gg["D1"] - r["D"].numpy()).max() < 1e-9
 
 
-def test_stored_and_on_the_fly_agree_c1(cd):
+@pytest.mark.parametrize("pm", [0, 1])
+def test_stored_and_on_the_fly_agree_c1(cd, pm):
     s = make_system(1)
     dL = make_displacements(s)
     gold = json.load(open(os.path.join(HERE, "golden", "c1.json")))
     a = run(cd, s, dL, ladder=cd.LADDER_STORED)
-    b = run(cd, s, dL, ladder=cd.LADDER_OTF, ladder_batch_gb=0.01)
+    b = run(cd, s, dL, ladder=cd.LADDER_OTF, ladder_batch_gb=0.01,
+            ladder_pm=pm)
     assert a["mode"] == cd.LADDER_STORED and b["mode"] == cd.LADDER_OTF
     assert abs(a["e"] - b["e"]) < 1e-11
     assert np.abs(a["g"] - b["g"]).max() < 1e-10
@@ -95,8 +100,9 @@ def test_stored_and_on_the_fly_agree_c1(cd):
     assert np.abs(b["g"] - np.array(gold["gradient"])).max() < 1e-8
 
 
+@pytest.mark.parametrize("pm", [0, 1])
 @pytest.mark.parametrize("prec", ["mixed", "tc"])
-def test_on_the_fly_ladder_tensor_core_schedules_c1(cd, prec):
+def test_on_the_fly_ladder_tensor_core_schedules_c1(cd, prec, pm):
     s = make_system(1)
     dL = make_displacements(s)
     gold = json.load(open(os.path.join(HERE, "golden", "c1.json")))
@@ -105,6 +111,7 @@ def test_on_the_fly_ladder_tensor_core_schedules_c1(cd, prec):
     o.precision = p
     o.ladder = cd.LADDER_OTF
     o.ladder_batch_gb = 0.05
+    o.ladder_pm = pm
     ctx = cd.init_from_system(s, options=o)
     e, g = cd.gradient(ctx, dL)
     cd.cd_ccsd_free(ctx)
@@ -123,9 +130,10 @@ def test_fused_float_slice_ladder_with_empty_cholesky_irrep(cd):
     dL = make_displacements(s, 3)
     r = oracle_run(s)
     G_or = pack_dense(s, r["G"].numpy())
-    for batch_gb in (0.0013, 2.0):
+    for batch_gb, pm in ((0.0013, 0), (2.0, 0), (0.0013, 1), (2.0, 1)):
         gg = run(cd, s, dL, ladder=cd.LADDER_OTF, ladder_batch_gb=batch_gb,
-                 precision=cd.PREC_TC, conv_tol=1e-10, energy_tol=1e-12)
+                 precision=cd.PREC_TC, conv_tol=1e-10, energy_tol=1e-12,
+                 ladder_pm=pm)
         assert gg["mode"] == cd.LADDER_OTF
         assert abs(gg["e"] - r["cc"]["E_corr"]) <= 1e-8
         assert np.abs(gg["g"] - dL @ G_or).max() <= 1e-6
