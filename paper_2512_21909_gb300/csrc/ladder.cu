@@ -590,12 +590,21 @@ void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
   ladder_reserve(need);
   const int h = dims_.h;
   const Layout& LL = L->lay;
+  // dL alone (the density sweep): with pair-symmetric dR and T, dW is
+  // invariant under the joint swap (ab,cd) -> (ba,dc) and both give the same
+  // dL terms, so only the batches with ga >= gb run, those with ga > gb at
+  // twice the weight (the +/- ladder's symmetry assumption)
+  const bool half = ladder_pm_ && !dT;
   for (const LadBatch& b : bs) {
+    const int gbb = b.ga ^ b.G;
+    if (half && b.ga < gbb) continue;
+    const double wgt = half && b.ga > gbb ? 2.0 : 1.0;
     release_scratch();   // stream order: the previous batch is queued
-    fl += ladder_build(b, L);
     const double fapply =
         2.0 * (double)b.rows * T->lay.ncol[b.G] * T->lay.nrow[b.G];
     if (dT) {
+      // the (ab|cd) rows are needed for dT only
+      fl += ladder_build(b, L);
       ladder_apply_batch(b, alpha, dR, dT);
       fl += fapply;
     }
@@ -624,7 +633,7 @@ void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
       check_block(g, dR->d, RL.size, T->d, T->lay.size, lad_w_, lad_n_);
       const Mat ma{dR->d, &RL, false, dR};
       const Mat mb{T->d, &T->lay, false, T};
-      run_gemms(&g, 1, ma, mb, alpha, 0.0);
+      run_gemms(&g, 1, ma, mb, alpha * wgt, 0.0);
     }
     ladder_perm(b, true, lad_w_, lad_x_);        // dX_gc[(a,c),(b,d)]
     GemmProb p1[GEMM_MAXPROB], p2[GEMM_MAXPROB];
