@@ -600,8 +600,10 @@ def run_ours(args, rank, ws):
         "ladder": {"seconds_per_step": lad[0], "flops_per_step": lad[1],
                    "tflops": lad[1] / lad[0] / 1e12 if lad[0] > 0 else None,
                    "share_of_step": lad[0] / t50,
-                   "note": "nominal flops of the ladder products, (ac|bd) "
-                           "builds from L^P_ab and their adjoints"},
+                   "note": "flops of the ladder products as executed "
+                           "(with the +/- packing: over canonical ij, ab, cd "
+                           "pairs, about a quarter of the plain map's), the "
+                           "(ac|bd) builds from L^P_ab and their adjoints"},
         "kernel_classes": classes,
         "roofline": roofline,
         "rooflines": roof,
