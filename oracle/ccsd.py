@@ -70,39 +70,46 @@ def dressed_fock(hh, Lh, o):
             - einsum("Ppk,Pkq->pq", Lh[:, :, :o], Lh[:, :o, :]))
 
 
-def ladder_block(t2, vv, a0: int, a1: int):
+def ladder_block(t2, vv, a0: int, a1: int, ein=None):
     """Rows a0 <= a < a1 of the ladder: (ac|bd) for that block of a, then
     sum_cd t[i,j,c,d] (ac|bd)."""
-    W = einsum("Pac,Pbd->acbd", vv[:, a0:a1], vv)        # (ac|bd), a in block
-    return einsum("ijcd,acbd->ijab", t2, W)
+    if ein is None:
+        W = einsum("Pac,Pbd->acbd", vv[:, a0:a1], vv)    # (ac|bd), a in block
+        return einsum("ijcd,acbd->ijab", t2, W)
+    W = ein("Pac,Pbd->acbd", vv[:, a0:a1], vv, ranges={"a": (a0, a1)})
+    return ein("ijcd,acbd->ijab", t2, W, ranges={"a": (a0, a1)})
 
 
-def ladder(t2, vv):
+def ladder(t2, vv, ein=None):
     """sum_cd t[i,j,c,d] (ac|bd), (ac|bd) = sum_P vv[P,a,c] vv[P,b,d]."""
     v = vv.shape[1]
     if v == 0:
         return torch.zeros_like(t2)
     blk = max(1, min(v, int(2.0e7 // max(1, v ** 3))))
     if blk >= v:
-        return ladder_block(t2, vv, 0, v)
+        return ladder_block(t2, vv, 0, v, ein)
     parts = []
     for a0 in range(0, v, blk):
         a1 = min(v, a0 + blk)
         if torch.is_grad_enabled():
-            parts.append(checkpoint(ladder_block, t2, vv, a0, a1,
+            parts.append(checkpoint(ladder_block, t2, vv, a0, a1, ein,
                                     use_reentrant=False))
         else:
-            parts.append(ladder_block(t2, vv, a0, a1))
+            parts.append(ladder_block(t2, vv, a0, a1, ein))
     return torch.cat(parts, dim=2)
 
 
-def residual(t1, t2, h, L, o):
+def residual(t1, t2, h, L, o, ein=None):
     """Closed-shell CCSD residuals and total energy.
 
     Returns (R1[i,a], R2[i,j,a,b], E) where E = <0|exp(-T) H exp(T)|0> is the
     total energy (reference + correlation).  t2 is symmetrised first, so the
     function is defined on the physical (symmetric) amplitude manifold.
+    `ein` replaces torch.einsum in the contractions below (None: the dense
+    einsum; oracle.blocked.irrep_einsum: the same products over the
+    symmetry-allowed blocks only).
     """
+    einsum = torch.einsum if ein is None else ein
     n = h.shape[0]
     t2 = sym2(t2)
     Lh, hh = dress(L, h, t1, o)
@@ -127,7 +134,7 @@ def residual(t1, t2, h, L, o):
 
     # ---- doubles
     R2 = g_vovo.permute(1, 3, 0, 2)                                # (ai|bj)
-    R2 = R2 + ladder(t2, vv)                                       # PPL
+    R2 = R2 + ladder(t2, vv, ein)                                  # PPL
     W = g_oooo + einsum("ijcd,kcld->kilj", t2, g_ovov)             # hole-hole
     R2 = R2 + einsum("klab,kilj->ijab", t2, W)
     # rings: the spin-orbital term P(ij)P(ab) sum_me t_im^ae W_mbej integrated

@@ -30,8 +30,9 @@ from .model import DT, fock
 from .ccsd import residual, denominators, DIIS, pack_amps, unpack_amps, sym2
 
 
-def lagrangian(t1, t2, l1, l2, h, L, o):
-    R1, R2, E = residual(t1, t2, h, L, o)
+def lagrangian(t1, t2, l1, l2, h, L, o, ein=None):
+    """Lag at (t, lambda); `ein` as in oracle.ccsd.residual."""
+    R1, R2, E = residual(t1, t2, h, L, o, ein)
     return E + (l1 * R1).sum() + (l2 * R2).sum()
 
 
