@@ -337,6 +337,27 @@ cdcc_status cdcc_contract_dL_noalloc(const double *gamma, const double *dL,
  * virtual range).                                                         */
 cdcc_status cdcc_get_amplitudes(cdcc_ctx *ctx, int which, double *out);
 
+/* Index tables of the +/- packed on-the-fly ladder (Sec. 2.3), for tests
+ * and inspection: HOST ONLY, no device work, no context.  The doubles
+ * amplitudes of nirrep irreps (1, 2, 4, 8) with nocc_irrep[g] occupied and
+ * nvir_irrep[g] virtual orbitals per irrep are stored per pair irrep G as a
+ * row-major block, rows (i,j) (i of irrep gi, sub-blocks by gi), columns
+ * (c,d) likewise; batch_gb bounds the FP64 (ab|cd) rows of one batch.
+ * Canonical pairs (p,q): irrep(p) > irrep(q), or the same irrep and p >= q.
+ * For every G with canonical pairs, out receives
+ *   G, uo, uv, nbatch, nrow(G), ncol(G),
+ *   row of (i,j)[uo], row of (j,i)[uo]       canonical occupied pairs,
+ *   column of (c,d)[uv], column of (d,c)[uv] canonical virtual pairs,
+ * then per row batch (a in [a0,a1) of irrep ga >= gb = ga^G)
+ *   ga, a0, a1, nv, row in the batch[nv], column of (a,b)[nv],
+ *   column of (b,a) or -1 when a == b[nv]
+ * (all int32, offsets inside the block).  *len = number of int32 written
+ * (or needed, with out = NULL).  Errors: CDCC_EINVAL for bad arguments or
+ * offsets beyond 32 bits, CDCC_ENOMEM when cap < *len.                    */
+cdcc_status cdcc_ladder_pm_tables(int nirrep, const int32_t *nocc_irrep,
+                                  const int32_t *nvir_irrep, double batch_gb,
+                                  int32_t *out, int64_t cap, int64_t *len);
+
 /* Wall-clock seconds of the last ccsd / lambda / density / contract_dL
  * phases (device time of the stream, CUDA events). */
 cdcc_status cdcc_phase_times(cdcc_ctx *ctx, double *t4);

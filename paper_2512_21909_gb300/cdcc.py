@@ -351,6 +351,50 @@ def cd_two_step(npair, naux, B, tau, sigma=1e-2, qmax=1000, device=0,
     return pivots, vectors, stats
 
 
+def ladder_pm_tables(nocc_irrep, nvir_irrep, batch_gb=2.0):
+    """Index tables of the +/- packed ladder (include/cdcc.h,
+    cdcc_ladder_pm_tables; host only).  Returns {G: dict(uo, uv, nrow, ncol,
+    r1, r2, c1, c2, batches=[dict(ga, a0, a1, lr, y1, y2)])}."""
+    lib = load()
+    lib.cdcc_ladder_pm_tables.argtypes = [
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+        ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.cdcc_ladder_pm_tables.restype = ctypes.c_int
+    h = len(nocc_irrep)
+    no = np.ascontiguousarray(nocc_irrep, dtype=np.int32)
+    nv = np.ascontiguousarray(nvir_irrep, dtype=np.int32)
+    n = ctypes.c_int64(0)
+    args = (h, no.ctypes.data_as(ctypes.c_void_p),
+            nv.ctypes.data_as(ctypes.c_void_p), float(batch_gb))
+    st = lib.cdcc_ladder_pm_tables(*args, None, 0, ctypes.byref(n))
+    if st != CDCC_OK:
+        raise CdccError(st, "cdcc_ladder_pm_tables")
+    out = np.zeros(max(1, n.value), np.int32)
+    st = lib.cdcc_ladder_pm_tables(*args, out.ctypes.data_as(ctypes.c_void_p),
+                                   int(out.size), ctypes.byref(n))
+    if st != CDCC_OK:
+        raise CdccError(st, "cdcc_ladder_pm_tables")
+    res, k = {}, 0
+    while k < n.value:
+        G, uo, uv, nb, nrow, ncol = (int(x) for x in out[k:k + 6])
+        k += 6
+        e = dict(uo=uo, uv=uv, nrow=nrow, ncol=ncol,
+                 r1=out[k:k + uo], r2=out[k + uo:k + 2 * uo])
+        k += 2 * uo
+        e["c1"], e["c2"] = out[k:k + uv], out[k + uv:k + 2 * uv]
+        k += 2 * uv
+        e["batches"] = []
+        for _ in range(nb):
+            ga, a0, a1, m = (int(x) for x in out[k:k + 4])
+            k += 4
+            e["batches"].append(dict(ga=ga, a0=a0, a1=a1,
+                                     lr=out[k:k + m], y1=out[k + m:k + 2 * m],
+                                     y2=out[k + 2 * m:k + 3 * m]))
+            k += 3 * m
+        res[G] = e
+    return res
+
+
 def cdcc_error_estimate(ctx, dL=None, nx=None, x_irrep=None):
     """(dE, dg[nx]): change of E and g caused by the schedule's reduced
     precision, measured against FP64 at the converged t and lambda."""

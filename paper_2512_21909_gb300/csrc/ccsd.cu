@@ -1437,6 +1437,67 @@ void free_ctx(cdcc_ctx* c) {
 
 extern "C" {
 
+cdcc_status cdcc_ladder_pm_tables(int nirrep, const int32_t* nocc_irrep,
+                                  const int32_t* nvir_irrep, double batch_gb,
+                                  int32_t* out, int64_t cap, int64_t* len) {
+  if (!nocc_irrep || !nvir_irrep || !len || !(batch_gb > 0) ||
+      !std::isfinite(batch_gb))
+    return CDCC_EINVAL;
+  if (nirrep != 1 && nirrep != 2 && nirrep != 4 && nirrep != 8)
+    return CDCC_EINVAL;
+  try {
+    Dims d;
+    d.h = nirrep;
+    for (int g = 0; g < nirrep; ++g) {
+      if (nocc_irrep[g] < 0 || nvir_irrep[g] < 0 || nocc_irrep[g] > 4096 ||
+          nvir_irrep[g] > 4096)
+        return CDCC_EINVAL;
+      d.n[SO][g] = nocc_irrep[g];
+      d.n[SV][g] = nvir_irrep[g];
+    }
+    Layout TL;
+    TL.rank = 4;
+    TL.sp[0] = SO;
+    TL.sp[1] = SO;
+    TL.sp[2] = SV;
+    TL.sp[3] = SV;
+    TL.split = 2;
+    TL.gtot = 0;
+    TL.build(d);
+    PmPlan P;
+    std::vector<int> tab;
+    pm_host_tables(TL, d, (int64_t)std::min(batch_gb * 1e9, 1e15), P, tab);
+    std::vector<int32_t> o;
+    for (int G = 0; G < nirrep; ++G) {
+      if (P.uo[G] == 0 || P.uv[G] == 0) continue;
+      int nb = 0;
+      for (const PmBatch& pb : P.batches) nb += pb.b.G == G;
+      o.insert(o.end(), {G, P.uo[G], P.uv[G], nb, (int32_t)TL.nrow[G],
+                         (int32_t)TL.ncol[G]});
+      o.insert(o.end(), tab.begin() + P.orow[G],
+               tab.begin() + P.orow[G] + 2 * P.uo[G]);
+      o.insert(o.end(), tab.begin() + P.vcol[G],
+               tab.begin() + P.vcol[G] + 2 * P.uv[G]);
+      for (const PmBatch& pb : P.batches) {
+        if (pb.b.G != G) continue;
+        o.insert(o.end(), {pb.b.ga, pb.b.a0, pb.b.a1, pb.nv});
+        o.insert(o.end(), tab.begin() + pb.vrow,
+                 tab.begin() + pb.vrow + 3 * pb.nv);
+      }
+    }
+    *len = (int64_t)o.size();
+    if (out) {
+      if (cap < (int64_t)o.size()) return CDCC_ENOMEM;
+      std::memcpy(out, o.data(), o.size() * sizeof(int32_t));
+    }
+    return CDCC_OK;
+  } catch (const EngineError&) {
+    return CDCC_EINVAL;
+  } catch (const std::bad_alloc&) {
+    return CDCC_ENOMEM;
+  }
+}
+
 void cdcc_default_options(cdcc_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));

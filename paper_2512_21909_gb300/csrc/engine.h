@@ -81,6 +81,42 @@ class EngineError : public std::exception {
   std::string msg;
 };
 
+// On-the-fly ladder row batch: the (ab|cd) rows (a,b) with a in [a0,a1) of
+// irrep ga and b of irrep ga^G, for the pair irrep G.
+struct LadBatch {
+  int G, ga, a0, a1;   // pair irrep, irrep of a, a range (local indices)
+  int64_t rows;        // (a,b) rows = (a1 - a0) * n_v(ga ^ G)
+};
+// row batches of a doubles layout {SO,SO,SV,SV}/2, at most batch_bytes of
+// FP64 rows each (host only)
+std::vector<LadBatch> ladder_batch_list(const Layout& TL, const Dims& d,
+                                        int64_t batch_bytes);
+
+// Index tables of the +/- packed ladder (ladder_pm.cu) for one doubles
+// layout: per pair irrep G the canonical occupied pairs (rows of (i,j) and
+// (j,i), [2][uo] at orow[G]) and virtual pairs (columns of (c,d) and (d,c),
+// [2][uv] at vcol[G]); per row batch with ga >= gb its canonical (a,b) rows
+// ([3][nv] at vrow: row in the batch, Y columns of (a,b) and (b,a) or -1).
+// Offsets are 32-bit, inside the DPD block of G.
+struct PmBatch {
+  LadBatch b;
+  int nv;          // canonical (a,b) rows of the batch
+  int64_t vrow;    // offset of its [3][nv] table
+};
+struct PmPlan {
+  std::string key;
+  int uo[MAXIRR] = {}, uv[MAXIRR] = {};
+  int64_t orow[MAXIRR] = {}, vcol[MAXIRR] = {};   // offsets in the table
+  std::vector<PmBatch> batches;
+  int* d_tab = nullptr;   // the table on the device (Engine::pm_plan)
+  size_t bytes = 0;
+  int64_t max_a = 0, max_w = 0;   // doubles of A+- and of a batch's W+-
+};
+// fill P (without d_tab) and the host table (host only; throws EngineError
+// when an offset does not fit in 32 bits)
+void pm_host_tables(const Layout& TL, const Dims& d, int64_t batch_bytes,
+                    PmPlan& P, std::vector<int>& tab);
+
 class Engine {
  public:
   Engine(const Dims& d, cudaStream_t st, DevAlloc al);
@@ -287,10 +323,6 @@ class Engine {
                         const Mat& mq, double alpha, double beta);
 
   // on-the-fly ladder
-  struct LadBatch {
-    int G, ga, a0, a1;   // pair irrep, irrep of a, a range (local indices)
-    int64_t rows;        // (a,b) rows = (a1 - a0) * n_v(ga ^ G)
-  };
   std::vector<LadBatch> ladder_batches(const Layout& TL);
   double ladder_build(const LadBatch& b, Tensor* L);   // -> lad_w_
   // float-slice arithmetic: the build GEMM writes the BF16 slices of the
@@ -334,20 +366,6 @@ class Engine {
   void ladder_lin_apply(int which, double alpha, Tensor* X, Tensor* LW,
                         bool stored, Tensor* Y);
   // +/- packed ladder: index tables per layout (device, one allocation)
-  struct PmBatch {
-    LadBatch b;
-    int nv;          // canonical (a,b) rows of the batch
-    int64_t vrow;    // offset of its [3][nv] table in d_tab
-  };
-  struct PmPlan {
-    std::string key;
-    int uo[MAXIRR] = {}, uv[MAXIRR] = {};
-    int64_t orow[MAXIRR] = {}, vcol[MAXIRR] = {};   // offsets in d_tab
-    std::vector<PmBatch> batches;
-    int* d_tab = nullptr;
-    size_t bytes = 0;
-    int64_t max_a = 0, max_w = 0;   // doubles of A+- and of a batch's W+-
-  };
   PmPlan pm_;
   bool ladder_pm_ = false;
   double* pm_a_ = nullptr;   // A+ | A- of one pair irrep (FP64)

@@ -64,7 +64,12 @@ void check_block(const GemmProb& g, const double* a0, int64_t asz,
 
 }  // namespace
 
-std::vector<Engine::LadBatch> Engine::ladder_batches(const Layout& TL) {
+std::vector<LadBatch> Engine::ladder_batches(const Layout& TL) {
+  return ladder_batch_list(TL, dims_, ladder_batch_bytes);
+}
+
+std::vector<LadBatch> ladder_batch_list(const Layout& TL, const Dims& dims_,
+                                        int64_t ladder_batch_bytes) {
   std::vector<LadBatch> out;
   const int h = dims_.h;
   for (int G = 0; G < h; ++G) {
@@ -715,14 +720,11 @@ void Engine::ladder_adjoint(double alpha, Tensor* dR, Tensor* T, Tensor* L,
 // slices the BF16 slices of W+- are kept across applications (they depend
 // on L only), within the budget of ladder_keep_slices.
 
-const Engine::PmPlan& Engine::pm_plan(const Layout& TL) {
-  std::ostringstream ks;
-  ks << TL.key() << '/' << ladder_batch_bytes;
-  if (pm_.d_tab && pm_.key == ks.str()) return pm_;
-  if (pm_.d_tab) al.release(pm_.d_tab, pm_.bytes);
-  pm_ = PmPlan();
+void pm_host_tables(const Layout& TL, const Dims& dims_,
+                    int64_t batch_bytes, PmPlan& P, std::vector<int>& tab) {
+  P = PmPlan();
+  tab.clear();
   const int h = dims_.h;
-  std::vector<int> tab;
   auto off32 = [](int64_t v) {
     if (v < 0 || v > INT32_MAX)
       throw EngineError("ladder +/-: block offset beyond 32 bits");
@@ -758,20 +760,20 @@ const Engine::PmPlan& Engine::pm_plan(const Layout& TL) {
           c2.push_back(off32(o2 + (int64_t)d * nc + c));
         }
     }
-    pm_.uo[G] = (int)r1.size();
-    pm_.uv[G] = (int)c1.size();
-    pm_.orow[G] = (int64_t)tab.size();
+    P.uo[G] = (int)r1.size();
+    P.uv[G] = (int)c1.size();
+    P.orow[G] = (int64_t)tab.size();
     tab.insert(tab.end(), r1.begin(), r1.end());
     tab.insert(tab.end(), r2.begin(), r2.end());
-    pm_.vcol[G] = (int64_t)tab.size();
+    P.vcol[G] = (int64_t)tab.size();
     tab.insert(tab.end(), c1.begin(), c1.end());
     tab.insert(tab.end(), c2.begin(), c2.end());
-    pm_.max_a = std::max<int64_t>(pm_.max_a,
-                                  2 * (int64_t)r1.size() * (int64_t)c1.size());
+    P.max_a = std::max<int64_t>(P.max_a,
+                                2 * (int64_t)r1.size() * (int64_t)c1.size());
   }
-  for (const LadBatch& b : ladder_batches(TL)) {
+  for (const LadBatch& b : ladder_batch_list(TL, dims_, batch_bytes)) {
     const int G = b.G, ga = b.ga, gb = ga ^ G;
-    if (ga < gb || pm_.uo[G] == 0 || pm_.uv[G] == 0) continue;
+    if (ga < gb || P.uo[G] == 0 || P.uv[G] == 0) continue;
     const int na = dims_.n[SV][ga], nb = dims_.n[SV][gb];
     const int64_t oab = TL.csub[G * TL.ncode_c + ga];
     const int64_t oba = TL.csub[G * TL.ncode_c + gb];
@@ -792,9 +794,19 @@ const Engine::PmPlan& Engine::pm_plan(const Layout& TL) {
     tab.insert(tab.end(), lr.begin(), lr.end());
     tab.insert(tab.end(), y1.begin(), y1.end());
     tab.insert(tab.end(), y2.begin(), y2.end());
-    pm_.batches.push_back(pb);
-    pm_.max_w = std::max(pm_.max_w, 2 * (int64_t)pb.nv * pm_.uv[G]);
+    P.batches.push_back(pb);
+    P.max_w = std::max<int64_t>(P.max_w, 2 * (int64_t)pb.nv * P.uv[G]);
   }
+}
+
+const PmPlan& Engine::pm_plan(const Layout& TL) {
+  std::ostringstream ks;
+  ks << TL.key() << '/' << ladder_batch_bytes;
+  if (pm_.d_tab && pm_.key == ks.str()) return pm_;
+  if (pm_.d_tab) al.release(pm_.d_tab, pm_.bytes);
+  pm_ = PmPlan();
+  std::vector<int> tab;
+  pm_host_tables(TL, dims_, ladder_batch_bytes, pm_, tab);
   if (!tab.empty()) {
     pm_.bytes = tab.size() * sizeof(int);
     pm_.d_tab = (int*)al.alloc(pm_.bytes);
