@@ -144,15 +144,31 @@ struct Footprint {
   size_t bytes = 0, ladder_bytes = 0;
 };
 
+// canonical virtual pairs of pair irrep G (irrep(c) > irrep(d), or the same
+// irrep and c >= d): the columns of the +/- packed ladder
+int64_t canonical_pairs(const std::vector<int>& v, int h, int G) {
+  int64_t s = 0;
+  for (int g = 0; g < h; ++g) {
+    const int g2 = g ^ G;
+    if (g > g2) s += (int64_t)v[g] * v[g2];
+    if (g == g2) s += (int64_t)v[g] * (v[g] + 1) / 2;
+  }
+  return s;
+}
+
 Footprint footprint(const cdcc_job_desc& j, int precision, int ladder,
-                    double batch_gb, double perm_gb, double slices_gb) {
+                    double batch_gb, double perm_gb, double slices_gb,
+                    bool pm) {
   Footprint f;
   std::vector<int> o, v, q;
   if (!counts(j, o, v, q)) return f;
   const int h = j.nirrep;
   std::vector<int> n(h);
   for (int g = 0; g < h; ++g) n[g] = o[g] + v[g];
+  int64_t wpm = 0;   // W+ and W- elements of the +/- ladder
   for (int G = 0; G < h; ++G) {
+    const int64_t u = canonical_pairs(v, h, G);
+    wpm += 2 * u * u;
     f.t2 += pairs(o, o, h, G) * pairs(v, v, h, G);
     f.w += pairs(v, v, h, G) * pairs(v, v, h, G);
     f.ovvv += pairs(o, v, h, G) * pairs(v, v, h, G);
@@ -172,9 +188,9 @@ Footprint footprint(const cdcc_job_desc& j, int precision, int ladder,
   } else {
     lad = 5.5 * batch_gb * 1e9;
     // BF16 batch slices kept across applications (two slices, float
-    // schedules only)
+    // schedules only): of the (ab|cd) rows, or of W+ and W- when packed
     if (precision != CDCC_PREC_FP64 && slices_gb > 0)
-      lad += std::min(4.0 * (double)f.w, slices_gb * 1e9);
+      lad += std::min(4.0 * (double)(pm ? wpm : f.w), slices_gb * 1e9);
   }
   f.ladder_bytes = (size_t)lad;
   f.bytes = (size_t)(base + lad);
@@ -349,7 +365,7 @@ size_t cdcc_job_footprint(const cdcc_job_desc* job, int precision, int ladder,
   cdcc_options d;
   cdcc_default_options(&d);
   return footprint(*job, precision, ladder, batch_gb, d.perm_cache_gb,
-                   d.ladder_slices_gb)
+                   d.ladder_slices_gb, d.ladder_pm != 0)
       .bytes;
 }
 
@@ -450,7 +466,8 @@ cdcc_status cdcc_submit(cdcc_server* s, const cdcc_job_desc* d,
   // ladder mode from the job's size only
   const Footprint fs =
       footprint(j->desc(), s->opt.precision, CDCC_LADDER_STORED, 0.0,
-                s->opt.perm_cache_gb, s->opt.ladder_slices_gb);
+                s->opt.perm_cache_gb, s->opt.ladder_slices_gb,
+                s->opt.ladder_pm != 0);
   j->ladder = (double)fs.ladder_bytes <= s->sopt.stored_max_gb * 1e9
                   ? CDCC_LADDER_STORED
                   : CDCC_LADDER_OTF;
@@ -458,7 +475,8 @@ cdcc_status cdcc_submit(cdcc_server* s, const cdcc_job_desc* d,
     j->ladder = s->opt.ladder;
   const double bgb = s->opt.ladder_batch_gb > 0 ? s->opt.ladder_batch_gb : 2.0;
   j->est_bytes = footprint(j->desc(), s->opt.precision, j->ladder, bgb,
-                           s->opt.perm_cache_gb, s->opt.ladder_slices_gb)
+                           s->opt.perm_cache_gb, s->opt.ladder_slices_gb,
+                           s->opt.ladder_pm != 0)
                      .bytes;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stopping) return CDCC_ESTATE;

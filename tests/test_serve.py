@@ -132,11 +132,12 @@ def test_ladder_policy_depends_on_size_only():
     assert small.ladder == cdcc.LADDER_STORED
     assert big.ladder == cdcc.LADDER_OTF
     # the estimate grows with the stored (ab|cd) integrals: v^4 doubles,
-    # 36 bytes per element in TC; on the fly keeps their two BF16 slices
-    # (4 bytes per element) from one ladder application to the next
+    # 36 bytes per element in TC; on the fly keeps two BF16 slices of W+
+    # and W- (the +/- packed ladder: canonical pairs c >= d, 40*41/2 of
+    # them in C1) from one ladder application to the next
     st = footprint_bytes(big, cdcc.PREC_TC, cdcc.LADDER_STORED)
     otf = footprint_bytes(big, cdcc.PREC_TC, cdcc.LADDER_OTF, 0.0)
-    assert st - otf == int(8 * 40 ** 4 * 4.5) - 4 * 40 ** 4
+    assert st - otf == int(8 * 40 ** 4 * 4.5) - 8 * (40 * 41 // 2) ** 2
 
 
 def test_other_failures_are_reported_per_request():
