@@ -137,3 +137,22 @@ def test_fused_float_slice_ladder_with_empty_cholesky_irrep(cd):
         assert gg["mode"] == cd.LADDER_OTF
         assert abs(gg["e"] - r["cc"]["E_corr"]) <= 1e-8
         assert np.abs(gg["g"] - dL @ G_or).max() <= 1e-6
+
+
+@pytest.mark.parametrize("pm", [0, 1])
+def test_float_slice_ladder_without_kept_slices(cd, pm):
+    # the float-slice ladder when no batch slices may be kept
+    # (ladder_slices_gb = 0): the plain map builds each batch into the batch
+    # buffer, the +/- map multiplies its FP64 W+- through the generic
+    # tensor-core route; same oracle and tolerances as above
+    s = random_system([5, 4, 4, 3], [24, 20, 20, 16], [40, 0, 34, 30],
+                      seed=214, scale=0.15)
+    dL = make_displacements(s, 3)
+    r = oracle_run(s)
+    G_or = pack_dense(s, r["G"].numpy())
+    gg = run(cd, s, dL, ladder=cd.LADDER_OTF, ladder_batch_gb=0.0013,
+             precision=cd.PREC_TC, conv_tol=1e-10, energy_tol=1e-12,
+             ladder_pm=pm, ladder_slices_gb=0.0)
+    assert gg["mode"] == cd.LADDER_OTF
+    assert abs(gg["e"] - r["cc"]["E_corr"]) <= 1e-8
+    assert np.abs(gg["g"] - dL @ G_or).max() <= 1e-6
