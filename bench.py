@@ -41,6 +41,7 @@ WORKLOAD = {0: "c0: C1 o=4 v=20 nL=60, 6 displacements",
             2: "c2: C2v o=40 v=360 nL=1600, 24 displacements",
             3: "c3: D2h o=60 v=540 nL=2400, 36 displacements"}
 DTYPE = {"fp64": "f64", "mixed": "bf16x3+f64", "tc": "bf16x3+exact-slice"}
+PLAIN_LADDER = False   # --plain-ladder: cdcc_options.ladder_pm = 0
 # FP64 pipe of GB300 (not in the measured peaks): 2 DFMA per clock per SM
 # x 2 flop x 152 SMs x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
@@ -71,6 +72,9 @@ def parse():
     ap.add_argument("--no-linearize", action="store_true",
                     help="every accurate-phase iteration fully accurate "
                          "(cdcc_options.ladder_linearize = 0)")
+    ap.add_argument("--plain-ladder", action="store_true",
+                    help="the on-the-fly ladder without the +/- packing "
+                         "(cdcc_options.ladder_pm = 0)")
     ap.add_argument("--error-estimate", action="store_true",
                     help="after the timed steps, run cdcc_error_estimate "
                          "(one FP64 residual and density sweep, untimed)")
@@ -344,6 +348,7 @@ class Runner:
         o.device = self.dev
         o.precision = prec_code(cdcc, prec)
         o.ladder_linearize = 1 if linearize else 0
+        o.ladder_pm = 0 if PLAIN_LADDER else 1
         ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
                                 s.orb_irrep, s.eps, s.chol_irrep,
                                 self.L_d if Lsrc is None else Lsrc, options=o)
@@ -439,6 +444,8 @@ def run_ours(args, rank, ws):
     barrier(ws)
     cdcc.load()
     pk = peaks()
+    global PLAIN_LADDER
+    PLAIN_LADDER = bool(args.plain_ladder)
     lin = not args.no_linearize
     run = Runner(args.config, dev, args.symmetry_ignored)
     s, nx = run.s, run.nx
@@ -503,6 +510,7 @@ def run_ours(args, rank, ws):
         o = cdcc.cdcc_default_options()
         o.precision = prec_code(cdcc, args.precision)
         o.ladder_linearize = 1 if lin else 0
+        o.ladder_pm = 0 if PLAIN_LADDER else 1
         ctx = cdcc.cd_ccsd_init(s.nirrep, s.nocc, s.nvir, s.nchol,
                                 s.orb_irrep, s.eps, s.chol_irrep, run.L_d,
                                 options=o)
@@ -586,6 +594,7 @@ def run_ours(args, rank, ws):
                        else ""),
                    "precision": args.precision,
                    "ladder_linearize": lin,
+                   "ladder_pm": not PLAIN_LADDER,
                    "l2": "flushed between steps (512 MiB write); inputs "
                          "larger than L2",
                    "parallelism": "replicas" if ws > 1 else "1 GPU"},
