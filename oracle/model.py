@@ -11,7 +11,9 @@ for the model Hamiltonian:
         h_pq = eps_p delta_pq - sum_k [ 2 (pq|kk) - (pk|kq) ]
   * a displacement changes only the Cholesky vectors (L -> L + x dL/dx),
     h stays fixed ("FIXED_CORE"), the MOs are the basis (no relaxation, no
-    overlap derivative: the S^x and Z-vector terms of Eq. gradcc_mo vanish);
+    overlap derivative: the S^x and Z-vector terms of Eq. gradcc_mo vanish;
+    the variant with orbitals relaxed by the SCF condition is in
+    oracle/zvector.py);
   * the energy differentiated is E = E_ref + E_corr with
         E_ref = sum_i (h_ii + f_ii),   f = h + G(L).
 All functions take torch float64 tensors (dense, symmetry ignored).
