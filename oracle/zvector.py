@@ -133,7 +133,6 @@ def relaxation_density_eq(Z, L, o):
     """Gamma_Z^P written out: with f_ai = h_ai + sum_k [2 (ai|kk) -
     (ak|ki)], the derivative of sum_ai Z_ai f_ai with respect to L^P_pq,
     symmetrised in pq."""
-    n = L.shape[1]
     J = torch.einsum("Pkk->P", L[:, :o, :o])
     g = torch.zeros_like(L)
     g[:, o:, :o] += 2.0 * J[:, None, None] * Z[None]                # L_ai
@@ -141,7 +140,6 @@ def relaxation_density_eq(Z, L, o):
     g[:, :o, :o] += 2.0 * zl[:, None, None] * torch.eye(o, dtype=DT)  # L_kk
     g[:, o:, :o] -= torch.einsum("ai,Pki->Pak", Z, L[:, :o, :o])    # L_ak
     g[:, :o, :o] -= torch.einsum("ai,Pak->Pki", Z, L[:, o:, :o])    # L_ki
-    del n
     return 0.5 * (g + g.transpose(1, 2))
 
 
@@ -176,11 +174,8 @@ def relaxed_energy(h, L, o, tol=1e-13, e_tol=1e-14):
 def relaxed_gradient(r, h, L, o, dL):
     """Relaxed gradient from a lagrangian.run_all result r at (h, L):
     (g_rel[x], Z, Gamma_rel) with g_rel = <Gamma^P + Gamma_Z^P, dL_x>."""
-    t1, t2 = r["cc"]["t1"], r["cc"]["t2"]
-    l1, l2 = r["lam"]["l1"], r["lam"]["l2"]
     A = orbital_hessian(h, L, o)
     rhs = orbital_gradient(r["D"], r["G"], h, L, o)
     Z = z_vector(A, rhs)
     Grel = r["G"] + relaxation_density_eq(Z, L, o)
-    del t1, t2, l1, l2
     return torch.einsum("Ppq,xPpq->x", Grel, dL), Z, Grel

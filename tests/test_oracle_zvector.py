@@ -89,7 +89,6 @@ def test_planted_hessian_mistake_is_caught(monkeypatch):
     r = lagrangian.run_all(h, L, o, tol=1e-12, e_tol=1e-13)
     good = zvector.orbital_hessian_eq(T(s.eps), L, o)
     # the paper's bracket without its exchange parts
-    n = L.shape[1]
     Lvv, Loo, Lvo = L[:, o:, o:], L[:, :o, :o], L[:, o:, :o]
     bad = good + torch.einsum("Pea,Pim->aiem", Lvv, Loo) \
         + torch.einsum("Pei,Pam->aiem", Lvo, Lvo)
@@ -98,4 +97,3 @@ def test_planted_hessian_mistake_is_caught(monkeypatch):
     g, _, _ = zvector.relaxed_gradient(r, h, L, o, dL)
     fd = _fd(h, L, o, dL[0])
     assert abs(float(g[0]) - fd) > 1e-7
-    del n
