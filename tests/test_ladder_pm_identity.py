@@ -12,7 +12,8 @@ writes those formulas out with loops over small symmetry-blocked arrays and
 checks them against the plain contraction sum_cd X_{ij,cd} (ac|bd) for
 pair-symmetric X, including the diagonal pairs (i = j, a = b, c = d) whose
 weights a dropped factor would break, and checks that a planted sign error
-is caught.
+is caught.  The partial form for O(o^3 v^3) products (only ij and cd
+packed, the output pair unsymmetric) is pinned the same way.
 """
 import numpy as np
 
@@ -110,3 +111,51 @@ def test_planted_sign_error_is_caught():
     ref = np.einsum("ijcd,abcd->ijab", X, V)
     bad = _pm_ladder(oi, vi, X, V, sign=-1.0)
     assert np.abs(bad - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def _partial_pm(oi, vi, X, V):
+    """Partial +/- form (Sec. 2.5) of Y_{ij,mb} = sum_cd X_{ij,cd} V_{mb,cd}
+    for pair-symmetric X and a V without symmetry in (mb): canonical ij and
+    cd only, Y_ij = S+ + S-, Y_ji = S+ - S-, two products at half the
+    flops."""
+    no, nv = len(oi), len(vi)
+    Y = np.zeros((no, no) + V.shape[:2])
+    R = _canonical(oi)
+    C = _canonical(vi)
+    for G in range(max(oi.max(), vi.max()) + 1):
+        RG = [(i, j) for (i, j) in R if oi[i] ^ oi[j] == G]
+        CG = [(c, d) for (c, d) in C if vi[c] ^ vi[d] == G]
+        if not RG or not CG:
+            continue
+        Ap = np.array([[0.5 * (X[i, j, c, d] + X[i, j, d, c]) for c, d in CG]
+                       for i, j in RG])
+        Am = np.array([[0.5 * (X[i, j, c, d] - X[i, j, d, c]) for c, d in CG]
+                       for i, j in RG])
+        Wp = np.stack([V[:, :, c, d] + (V[:, :, d, c] if c != d else 0.0)
+                       for c, d in CG], axis=-1)
+        Wm = np.stack([V[:, :, c, d] - V[:, :, d, c] for c, d in CG],
+                      axis=-1)
+        Sp = np.einsum("ru,mbu->rmb", Ap, Wp)
+        Sm = np.einsum("ru,mbu->rmb", Am, Wm)
+        for r, (i, j) in enumerate(RG):
+            Y[i, j] += Sp[r] + Sm[r]
+            if i != j:
+                Y[j, i] += Sp[r] - Sm[r]
+    return Y
+
+
+def test_partial_pm_packing_reproduces_the_product():
+    # the O(o^3 v^3) product sum_cd tau_ij^cd (mc|bd) of the residual's
+    # T1 terms, in the partial +/- form
+    for seed, occ, vir, nq in [(1, [2, 1], [3, 2], [4, 3]),
+                               (2, [2, 1, 1, 1], [3, 2, 2, 1], [3, 2, 2, 2])]:
+        oi, vi, X, _ = _system(seed, occ, vir, nq)
+        rng = np.random.default_rng(seed)
+        # V[m,b,c,d] stands for (mc|bd); the identity uses only the pair
+        # symmetry of X, so any V with a block pattern will do
+        V = rng.standard_normal((len(oi), len(vi), len(vi), len(vi)))
+        V *= ((oi[:, None, None, None] ^ vi[None, :, None, None]) ==
+              (vi[None, None, :, None] ^ vi[None, None, None, :]))
+        ref = np.einsum("ijcd,mbcd->ijmb", X, V)
+        got = _partial_pm(oi, vi, X, V)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), seed
