@@ -138,6 +138,14 @@ typedef struct {
                                ab and cd (Sec. 2.3): two products over the
                                canonical pairs, a quarter of the flops of
                                the plain map (default 1; 0 = plain map)     */
+    int relaxed;            /* orbital relaxation (Sec. 2.5, Eq. z_vector):
+                               the orbitals follow the closed-shell SCF
+                               condition f_ai = 0 under a displacement;
+                               build_density solves the Z-vector equations
+                               and adds the relaxation term to Gamma^P, so
+                               contract_dL returns the relaxed gradient
+                               (CDCC_FIXED_CORE only; D stays the unrelaxed
+                               dLag/dh).  Default 0.                        */
 } cdcc_options;
 
 typedef struct cdcc_ctx cdcc_ctx;

@@ -44,7 +44,8 @@ class cdcc_options(ctypes.Structure):
                 ("ladder_linearize", ctypes.c_int),
                 ("perm_cache_gb", ctypes.c_double),
                 ("ladder_slices_gb", ctypes.c_double),
-                ("ladder_pm", ctypes.c_int)]
+                ("ladder_pm", ctypes.c_int),
+                ("relaxed", ctypes.c_int)]
 
 
 class CdccError(RuntimeError):

@@ -153,6 +153,7 @@ struct cdcc_ctx {
   unsigned int* d_err = nullptr;
   int iters_mixed[2] = {0, 0}, iters_fp64[2] = {0, 0};
   bool otf = false;   // ladder assembled on the fly (no stored W0)
+  int z_iters = 0;    // conjugate-gradient iterations of the Z-vector solve
 };
 
 namespace {
@@ -806,6 +807,7 @@ void run_lambda(cdcc_ctx* c, int* iters, double* resid) {
 
 void assemble_density(cdcc_ctx* c);
 void frozen_fock_correction(cdcc_ctx* c);
+void relax_density(cdcc_ctx* c);
 
 void run_density(cdcc_ctx* c, double* D1) {
   Engine& e = *c->eng;
@@ -820,6 +822,7 @@ void run_density(cdcc_ctx* c, double* D1) {
   e.set_precision(0);
   assemble_density(c);
   if (c->opt.fock_model == CDCC_FROZEN_FOCK) frozen_fock_correction(c);
+  if (c->opt.relaxed) relax_density(c);
   pt.stop();
   if (D1) {
     const int n = c->hd.n;
@@ -887,6 +890,125 @@ void frozen_fock_correction(cdcc_ctx* c) {
   e.axpy(1.0, e.adjoint(Lvv), "Pab", 1.0, Dg, "Pab");
   e.axpy(-0.5, Dg, "Ppq", 1.0, c->Gsym, "Ppq");
   e.axpy(-0.5, Dg, "Pqp", 1.0, c->Gsym, "Ppq");
+}
+
+// Orbital relaxation (Sec. 2.5, Eq. z_vector) of the relaxed model: the
+// orbitals follow the closed-shell SCF condition f_ai = 0 at every
+// displacement, so the gradient gains sum_ai Z_ai df_ai/dx with Z the
+// solution of the Z-vector equations
+//     sum_em A_ai,em Z_em = -2 W_ai,   W = [h, D] + sum_P [L^P, Gamma^P],
+//     A_ai,em = f_ae d_im - f_mi d_ae + 4 (ai|em) - (ae|im) - (am|ie)
+// (A is the bracket of Eq. z_vector written with the Fock blocks; it is
+// symmetric, so conjugate gradients solve the system with one Hessian
+// product per iteration through the Cholesky vectors).  Then
+//     Gamma^P += sym d/dL^P sum_ai Z_ai f_ai(L)
+// (one reverse sweep of a recorded evaluation, as in the frozen-Fock
+// correction).  D is left as the unrelaxed dLag/dh.
+void relax_density(cdcc_ctx* c) {
+  Engine& e = *c->eng;
+  Tensor *Loo = c->Loo, *Lov = c->Lov, *Lvo = c->Lvo, *Lvv = c->Lvv;
+  // blocks of the symmetric D and Gamma^P
+  Tensor* Doo = e.tensor("rx_Doo", {SO, SO}, 1);
+  Tensor* Dvo = e.tensor("rx_Dvo", {SV, SO}, 1);
+  Tensor* Dvv = e.tensor("rx_Dvv", {SV, SV}, 1);
+  e.axpy(1.0, c->D1s, "pq", 0.0, Doo, "pq");
+  e.axpy(1.0, c->D1s, "pq", 0.0, Dvo, "pq");
+  e.axpy(1.0, c->D1s, "pq", 0.0, Dvv, "pq");
+  Tensor* Goo = e.tensor("rx_Goo", {SQ, SO, SO}, 1);
+  Tensor* Gvo = e.tensor("rx_Gvo", {SQ, SV, SO}, 1);
+  Tensor* Gvv = e.tensor("rx_Gvv", {SQ, SV, SV}, 1);
+  e.axpy(1.0, c->Gsym, "Ppq", 0.0, Goo, "Ppq");
+  e.axpy(1.0, c->Gsym, "Ppq", 0.0, Gvo, "Ppq");
+  e.axpy(1.0, c->Gsym, "Ppq", 0.0, Gvv, "Ppq");
+  // W_ai = [h, D]_ai + sum_P [L^P, Gamma^P]_ai
+  Tensor* W = e.tensor("rx_W", {SV, SO}, 1);
+  e.contract(1.0, c->hvv, "ab", Dvo, "bi", 0.0, W, "ai");
+  e.contract(1.0, c->hvo, "aj", Doo, "ji", 1.0, W, "ai");
+  e.contract(-1.0, Dvv, "ab", c->hvo, "bi", 1.0, W, "ai");
+  e.contract(-1.0, Dvo, "aj", c->hoo, "ji", 1.0, W, "ai");
+  e.contract(1.0, Lvv, "Pab", Gvo, "Pbi", 1.0, W, "ai");
+  e.contract(1.0, Lvo, "Paj", Goo, "Pji", 1.0, W, "ai");
+  e.contract(-1.0, Gvv, "Pab", Lvo, "Pbi", 1.0, W, "ai");
+  e.contract(-1.0, Gvo, "Paj", Loo, "Pji", 1.0, W, "ai");
+  // Fock blocks f = h + G(L) (diag(eps) at the reference of the model)
+  Tensor* J = e.tensor("rx_J", {SQ}, 1);
+  e.contract(1.0, Loo, "Pkl", c->Ioo, "kl", 0.0, J, "P");
+  Tensor* Foo = e.tensor("rx_Foo", {SO, SO}, 1);
+  e.axpy(1.0, c->hoo, "ij", 0.0, Foo, "ij");
+  e.contract(2.0, Loo, "Pij", J, "P", 1.0, Foo, "ij");
+  e.contract(-1.0, Loo, "Pik", Loo, "Pkj", 1.0, Foo, "ij");
+  Tensor* Fvv = e.tensor("rx_Fvv", {SV, SV}, 1);
+  e.axpy(1.0, c->hvv, "ab", 0.0, Fvv, "ab");
+  e.contract(2.0, Lvv, "Pab", J, "P", 1.0, Fvv, "ab");
+  e.contract(-1.0, Lvo, "Pak", Lov, "Pkb", 1.0, Fvv, "ab");
+  // A p through the Cholesky vectors
+  Tensor* X = e.tensor("rx_X", {SQ}, 1);
+  Tensor* Y = e.tensor("rx_Y", {SQ, SO, SV}, 1);
+  Tensor* Q = e.tensor("rx_Q", {SQ, SO, SO}, 1);
+  auto hess = [&](Tensor* p, Tensor* Ap) {
+    e.contract(1.0, Fvv, "ae", p, "ei", 0.0, Ap, "ai");
+    e.contract(-1.0, p, "am", Foo, "mi", 1.0, Ap, "ai");
+    e.contract(1.0, Lvo, "Pem", p, "em", 0.0, X, "P");
+    e.contract(4.0, Lvo, "Pai", X, "P", 1.0, Ap, "ai");
+    e.contract(1.0, Loo, "Pim", p, "em", 0.0, Y, "Pie");
+    e.contract(-1.0, Lvv, "Pae", Y, "Pie", 1.0, Ap, "ai");
+    e.contract(1.0, Lov, "Pie", p, "em", 0.0, Q, "Pim");
+    e.contract(-1.0, Lvo, "Pam", Q, "Pim", 1.0, Ap, "ai");
+  };
+  Tensor* S = e.tensor("rx_S", {}, 0);
+  auto dot = [&](Tensor* a, Tensor* b) {
+    e.contract(1.0, a, "ai", b, "ai", 0.0, S, "");
+    return scalar(c, S);
+  };
+  Tensor* Z = e.tensor("rx_Z", {SV, SO}, 1);
+  Tensor* r = e.tensor("rx_r", {SV, SO}, 1);
+  Tensor* p = e.tensor("rx_p", {SV, SO}, 1);
+  Tensor* Ap = e.tensor("rx_Ap", {SV, SO}, 1);
+  e.zero(Z);
+  e.axpy(-2.0, W, "ai", 0.0, r, "ai");      // r = b - A*0, b = -2W
+  e.axpy(1.0, r, "ai", 0.0, p, "ai");
+  double rr = dot(r, r);
+  const double bb = rr;
+  const double tol2 = 1e-26 * std::max(bb, 1e-300);
+  int it = 0;
+  while (rr > tol2) {
+    if (++it > 500)
+      throw StatusError(CDCC_ENOCONV, "Z-vector equations did not converge");
+    hess(p, Ap);
+    const double pAp = dot(p, Ap);
+    if (!(pAp > 0) || !std::isfinite(pAp))
+      throw StatusError(CDCC_ENUMERIC,
+                        "Z-vector: the orbital Hessian is not positive");
+    const double alpha = rr / pAp;
+    e.axpy(alpha, p, "ai", 1.0, Z, "ai");
+    e.axpy(-alpha, Ap, "ai", 1.0, r, "ai");
+    const double rn = dot(r, r);
+    e.axpy(1.0, r, "ai", rn / rr, p, "ai");
+    rr = rn;
+  }
+  // Gamma^P += sym d/dL^P <Z, f_vo(L)>, f_vo = h_vo + 2 L_vo J - L_vk L_ko
+  e.clear_tape();
+  c->tape_ready = false;
+  e.record(true);
+  Tensor* Jr = e.tensor("rx_Jr", {SQ}, 1);
+  e.contract(1.0, Loo, "Pkl", c->Ioo, "kl", 0.0, Jr, "P");
+  Tensor* Gf = e.tensor("rx_Gf", {SV, SO}, 1);
+  e.contract(2.0, Lvo, "Pai", Jr, "P", 0.0, Gf, "ai");
+  e.contract(-1.0, Lvo, "Pak", Loo, "Pki", 1.0, Gf, "ai");
+  Tensor* EZ = e.tensor("rx_EZ", {}, 0);
+  e.contract(1.0, Z, "ai", Gf, "ai", 0.0, EZ, "");
+  e.record(false);
+  e.backward({{EZ, nullptr}}, TAG_L);
+  e.clear_tape();
+  Tensor* Dg = e.tensor("rx_dG", {SQ, SA, SA}, 1);
+  e.zero(Dg);
+  e.axpy(1.0, e.adjoint(Loo), "Pij", 1.0, Dg, "Pij");
+  e.axpy(1.0, e.adjoint(Lov), "Pia", 1.0, Dg, "Pia");
+  e.axpy(1.0, e.adjoint(Lvo), "Pai", 1.0, Dg, "Pai");
+  e.axpy(1.0, e.adjoint(Lvv), "Pab", 1.0, Dg, "Pab");
+  e.axpy(0.5, Dg, "Ppq", 1.0, c->Gsym, "Ppq");
+  e.axpy(0.5, Dg, "Pqp", 1.0, c->Gsym, "Ppq");
+  c->z_iters = it;
 }
 
 // Gamma^P and D from the adjoints left by the density sweep.
@@ -1100,6 +1222,7 @@ void run_error_estimate(cdcc_ctx* c, int nx, const int32_t* x_irrep,
              TAG_L | TAG_H);
   assemble_density(c);
   if (c->opt.fock_model == CDCC_FROZEN_FOCK) frozen_fock_correction(c);
+  if (c->opt.relaxed) relax_density(c);
   if (nx > 0) run_contract(c, nx, x_irrep, dL, g64.data());
   for (int x = 0; x < nx; ++x) dg[x] = std::fabs(g64[x] - g0[x]);
   CK(cudaMemcpyAsync(c->Gsym->d, keepG->d, (size_t)ng * 8,
@@ -1516,6 +1639,7 @@ void cdcc_default_options(cdcc_options* o) {
   o->perm_cache_gb = 32.0;
   o->ladder_slices_gb = 48.0;
   o->ladder_pm = 1;
+  o->relaxed = 0;
 }
 
 cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
@@ -1538,6 +1662,11 @@ cdcc_status cd_ccsd_init(cdcc_ctx** out, int nirrep, int nocc, int nvir,
         c->opt.fock_model > CDCC_FROZEN_FOCK)
       throw StatusError(CDCC_EINVAL,
                         "unknown precision, ladder mode or Fock model");
+    if (c->opt.relaxed != 0 &&
+        (c->opt.relaxed != 1 || c->opt.fock_model != CDCC_FIXED_CORE))
+      throw StatusError(CDCC_EINVAL,
+                        "orbital relaxation is defined for the fixed-core "
+                        "model only (relaxed = 0 or 1)");
     init_ctx(c, nirrep, nocc, nvir, nchol, orb_irrep, eps, chol_irrep, L);
   });
   *out = c;  // also on error, so that cdcc_last_error can be read
