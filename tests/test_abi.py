@@ -117,3 +117,17 @@ def test_two_step_cd_rejects_bad_arguments(lib, kw):
         cdcc.cd_two_step(npair, naux, B, kw.get("tau", 1e-6),
                          sigma=kw.get("sigma", 1e-2), qmax=kw.get("qmax", 10))
     assert e.value.status == cdcc.CDCC_EINVAL
+
+
+@pytest.mark.parametrize("relaxed,frozen", [(2, False), (1, True)])
+def test_relaxed_option_rejected_on_host(lib, relaxed, frozen):
+    # orbital relaxation is defined for the fixed-core model only
+    s = random_system([1, 1], [2, 2], [3, 3], seed=1)
+    o = cdcc.cdcc_default_options()
+    assert o.relaxed == 0
+    o.relaxed = relaxed
+    if frozen:
+        o.fock_model = cdcc.FROZEN_FOCK
+    with pytest.raises(cdcc.CdccError) as ei:
+        _init(s, options=o)
+    assert ei.value.status == cdcc.CDCC_EINVAL
