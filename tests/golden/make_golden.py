@@ -7,6 +7,8 @@ t2 and lambda2 elements (packed / dense indices with values).
 
     python tests/golden/make_golden.py 1        # writes tests/golden/c1.json
     python tests/golden/make_golden.py serving  # writes tests/golden/serving.json
+    python tests/golden/make_golden.py relaxed1 # writes c1_relaxed.json
+(relaxed: the gradient of the orbital-relaxed model, oracle/zvector.py.)
 """
 from __future__ import annotations
 
@@ -54,6 +56,31 @@ def golden(idx: int, nsample: int = 64):
     )
 
 
+def golden_relaxed(idx: int):
+    """Relaxed gradient (Sec. 2.5, Eq. z_vector) of the orbital-relaxed
+    model on workload idx: every displacement, the Z-vector norm and its
+    largest elements."""
+    from oracle import zvector
+    s = make_system(idx)
+    o = s.nocc
+    L = torch.as_tensor(unpack_dense(s, s.L))
+    h = model.core_from_eps(torch.as_tensor(s.eps), L, o)
+    t0 = time.time()
+    r = lagrangian.run_all(h, L, o, tol=1e-11, e_tol=1e-13)
+    dL = make_displacements(s)
+    dLd = torch.as_tensor(np.stack([unpack_dense(s, x) for x in dL]))
+    g, Z, _ = zvector.relaxed_gradient(r, h, L, o, dLd)
+    secs = time.time() - t0
+    Zf = Z.numpy().reshape(-1)
+    big = np.argsort(-np.abs(Zf))[:32]
+    return dict(
+        workload=s.name, cfg_index=idx, tol=1e-11, model="relaxed",
+        e_corr=r["cc"]["E_corr"], gradient=g.numpy().tolist(),
+        gradient_unrelaxed=(dL @ pack_dense(s, r["G"].numpy())).tolist(),
+        z_norm=float(np.linalg.norm(Zf)), z_index=big.tolist(),
+        z_value=Zf[big].tolist(), oracle_seconds=secs)
+
+
 def golden_serving(omax: int = 16, nx: int = 2):
     """FP64 oracle energy and gradient of every serving request with
     o <= omax (the first 64 requests of the serving workload)."""
@@ -83,6 +110,14 @@ if __name__ == "__main__":
         if a == "serving":
             out = golden_serving()
             path = os.path.join(HERE, "serving.json")
+            with open(path, "w") as f:
+                json.dump(out, f, indent=1)
+            print("wrote", path)
+            continue
+        if a.startswith("relaxed"):
+            idx = int(a[len("relaxed"):])
+            out = golden_relaxed(idx)
+            path = os.path.join(HERE, f"c{idx}_relaxed.json")
             with open(path, "w") as f:
                 json.dump(out, f, indent=1)
             print("wrote", path)

@@ -97,3 +97,23 @@ def test_planted_hessian_mistake_is_caught(monkeypatch):
     g, _, _ = zvector.relaxed_gradient(r, h, L, o, dL)
     fd = _fd(h, L, o, dL[0])
     assert abs(float(g[0]) - fd) > 1e-7
+
+
+def test_stored_relaxed_values_are_the_oracle_s():
+    # tests/golden/c0_relaxed.json (make_golden.py relaxed0) against a fresh
+    # oracle evaluation, and its unrelaxed part against c0.json
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    gold = json.load(open(os.path.join(here, "c0_relaxed.json")))
+    base = json.load(open(os.path.join(here, "c0.json")))
+    s = make_system(0)
+    o = s.nocc
+    L = T(unpack_dense(s, s.L))
+    h = model.core_from_eps(T(s.eps), L, o)
+    r = lagrangian.run_all(h, L, o, tol=1e-11, e_tol=1e-13)
+    dL = T(np.stack([unpack_dense(s, x) for x in make_displacements(s)]))
+    g, _, _ = zvector.relaxed_gradient(r, h, L, o, dL)
+    assert np.abs(g.numpy() - np.array(gold["gradient"])).max() < 1e-9
+    assert np.abs(np.array(gold["gradient_unrelaxed"])
+                  - np.array(base["gradient"])).max() < 1e-9
